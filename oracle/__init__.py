@@ -1,0 +1,168 @@
+"""CPU oracle of detector LUT generation and LUT-based image correction.
+
+TEST INFRASTRUCTURE ONLY: the plain, slow reference that the CUDA library is
+checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference arm may import it.  It shares no code
+with the CUDA path; the definitions it follows are stated in
+``lutc_oracle.c`` (steps L, P, H, S, C, A there).
+
+The C source is compiled with the host ``gcc`` on first use (or by
+:func:`build`) into ``oracle/_build/liblutc_oracle.so``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lutc_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liblutc_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (host gcc, plain -O2, single threaded)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp], check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        i32, i64, p = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+        lib.oracle_lut_entry.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, i64, i32]
+        lib.oracle_lut_entry.restype = i64
+        lib.oracle_lutgen.argtypes = [p, p, p, i32, i32, p]
+        lib.oracle_lutgen.restype = None
+        lib.oracle_apply_u16.argtypes = [p, i64, i32, i32, i32, p, p, i64]
+        lib.oracle_apply_u16.restype = None
+        lib.oracle_hist.argtypes = [p, i64, i32, i32, i32, p, p]
+        lib.oracle_hist.restype = None
+        lib.oracle_stretch.argtypes = [p, i32, p, p]
+        lib.oracle_stretch.restype = None
+        lib.oracle_compose.argtypes = [p, p, i32, i32, p]
+        lib.oracle_compose.restype = None
+        lib.oracle_apply_u8.argtypes = [p, i64, i32, i32, i32, p, p, i64]
+        lib.oracle_apply_u8.restype = None
+        lib.oracle_correct_image.argtypes = [p, i64, i32, i32, i32, i32, p, p, p, i32, p, i64, p, p, p]
+        lib.oracle_correct_image.restype = i32
+        _lib = lib
+    return _lib
+
+
+def _c(a: np.ndarray, dtype) -> np.ndarray:
+    a = np.asarray(a)
+    assert a.dtype == dtype, (a.dtype, dtype)
+    return a
+
+
+def _rows(img: np.ndarray):
+    """(height, width, pitch in elements) of a 2-D array with contiguous rows."""
+    assert img.ndim == 2 and img.strides[1] == img.itemsize
+    return img.shape[0], img.shape[1], img.strides[0] // img.itemsize
+
+
+def lut_entry(A: int, G: int, O: int, x: int, bits: int) -> int:
+    """One entry of the detector LUT (step L)."""
+    return int(_load().oracle_lut_entry(int(A), int(G), int(O), int(x), int(bits)))
+
+
+def lutgen(A, G, O, bits: int) -> np.ndarray:
+    """Detector LUT ``[ncols, 2^bits]`` uint16 (step L)."""
+    A = np.ascontiguousarray(_c(A, np.int32))
+    G = np.ascontiguousarray(_c(G, np.int32))
+    O = np.ascontiguousarray(_c(O, np.int32))
+    n = A.shape[0]
+    lut = np.empty((n, 1 << bits), np.uint16)
+    _load().oracle_lutgen(A.ctypes.data, G.ctypes.data, O.ctypes.data, n, bits, lut.ctypes.data)
+    return lut
+
+
+def apply_u16(img: np.ndarray, lut: np.ndarray, bits: int) -> np.ndarray:
+    """Detector-corrected band (step P)."""
+    img = _c(img, np.uint16)
+    h, w, pitch = _rows(img)
+    lut = np.ascontiguousarray(_c(lut, np.uint16))
+    assert lut.shape == (w, 1 << bits)
+    out = np.empty((h, w), np.uint16)
+    _load().oracle_apply_u16(img.ctypes.data, pitch, w, h, bits, lut.ctypes.data, out.ctypes.data, w)
+    return out
+
+
+def hist(img: np.ndarray, lut: np.ndarray, bits: int) -> np.ndarray:
+    """Histogram of corrected DN of one band (step H), 2^bits uint64 bins."""
+    img = _c(img, np.uint16)
+    h, w, pitch = _rows(img)
+    lut = np.ascontiguousarray(_c(lut, np.uint16))
+    assert lut.shape == (w, 1 << bits)
+    out = np.empty(1 << bits, np.uint64)
+    _load().oracle_hist(img.ctypes.data, pitch, w, h, bits, lut.ctypes.data, out.ctypes.data)
+    return out
+
+
+def stretch(hist_: np.ndarray, bits: int):
+    """(S uint8[2^bits], lo, hi) of one band's histogram (step S)."""
+    hist_ = np.ascontiguousarray(_c(hist_, np.uint64))
+    assert hist_.shape == (1 << bits,)
+    S = np.empty(1 << bits, np.uint8)
+    lohi = np.empty(2, np.int32)
+    _load().oracle_stretch(hist_.ctypes.data, bits, S.ctypes.data, lohi.ctypes.data)
+    return S, int(lohi[0]), int(lohi[1])
+
+
+def compose(lut: np.ndarray, S: np.ndarray, bits: int) -> np.ndarray:
+    """Composed per-column uint8 LUT (step C)."""
+    lut = np.ascontiguousarray(_c(lut, np.uint16))
+    S = np.ascontiguousarray(_c(S, np.uint8))
+    n = lut.shape[0]
+    out = np.empty((n, 1 << bits), np.uint8)
+    _load().oracle_compose(lut.ctypes.data, S.ctypes.data, n, bits, out.ctypes.data)
+    return out
+
+
+def apply_u8(img: np.ndarray, clut: np.ndarray, bits: int) -> np.ndarray:
+    """uint8 output band through a composed LUT (step A)."""
+    img = _c(img, np.uint16)
+    h, w, pitch = _rows(img)
+    clut = np.ascontiguousarray(_c(clut, np.uint8))
+    assert clut.shape == (w, 1 << bits)
+    out = np.empty((h, w), np.uint8)
+    _load().oracle_apply_u8(img.ctypes.data, pitch, w, h, bits, clut.ctypes.data, out.ctypes.data, w)
+    return out
+
+
+def correct_image(raster: np.ndarray, A, G, O, bits: int, stretch: bool = True, with_tables: bool = False):
+    """Whole correction of a planar raster ``[bands, height, width]``.
+
+    Returns the uint8 (stretch) or uint16 (detector only) raster, and with
+    ``with_tables`` also ``(hist [bands, 2^bits], S [bands, 2^bits], lohi [bands, 2])``.
+    """
+    raster = _c(raster, np.uint16)
+    assert raster.ndim == 3 and raster.strides[2] == 2
+    bands, h, w = raster.shape
+    pitch = raster.strides[1] // 2
+    assert raster.strides[0] == h * raster.strides[1], "bands must be stacked at height * pitch"
+    A = np.ascontiguousarray(_c(A, np.int32)).reshape(bands, w)
+    G = np.ascontiguousarray(_c(G, np.int32)).reshape(bands, w)
+    O = np.ascontiguousarray(_c(O, np.int32)).reshape(bands, w)
+    L = 1 << bits
+    out = np.empty((bands, h, w), np.uint8 if stretch else np.uint16)
+    hist_ = np.zeros((bands, L), np.uint64)
+    S = np.zeros((bands, L), np.uint8)
+    lohi = np.zeros((bands, 2), np.int32)
+    rc = _load().oracle_correct_image(raster.ctypes.data, pitch, w, h, bands, bits,
+                                      A.ctypes.data, G.ctypes.data, O.ctypes.data, int(bool(stretch)),
+                                      out.ctypes.data, w, hist_.ctypes.data, S.ctypes.data, lohi.ctypes.data)
+    if rc != 0:
+        raise MemoryError("oracle_correct_image could not allocate its tables")
+    if with_tables:
+        return out, (hist_, S, lohi)
+    return out
