@@ -1,0 +1,400 @@
+"""Benchmark of the fused LUT correction on GB300.
+
+One step = one ``lutc_correct_image`` (detector LUT evaluation, per-band
+histogram, 2/98 % stretch, composed uint8 gather) over the whole "scene"
+workload: 4 bands of 12000 x 12000 uint16 12-bit pixels, resident in HBM
+(1.15 GB in, 576 MB out per step: larger than the 129 MB L2, so no flush is
+needed between steps).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload scene|large14|tiny]
+  python bench.py --impl reference ...   # the CPU oracle, timed on a bounded sample
+
+With N > 1 (torchrun) every rank corrects its own scene (weak scaling, no
+data-path collective); the step time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import datetime
+import glob
+import hashlib
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Gpixel/s & % HBM peak (fused/batched vs plain); p50/p99 served latency"
+UNIT = "Gpixel/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1505_05655_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(os.path.basename(p).encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on this source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        e = t[workload][kernel]
+        if e.get("csrc") != csrc_hash():
+            return None
+        return float(e["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms in the background."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str | None):
+        self.proc = None
+        self.path = None
+        exe = shutil.which("nvidia-smi")
+        if not exe:
+            return
+        self.path = os.path.join("/tmp", "lutc_clocks_%d.csv" % os.getpid())
+        cmd = [exe, "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "100"]
+        if device_id:
+            cmd += ["-i", device_id]
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, t0: float, t1: float):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    rows.append((ts, float(parts[1]), float(parts[2]), parts[3:]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        inside = [r for r in rows if t0 - 0.15 <= r[0] <= t1 + 0.15]
+        if not inside:
+            inside = sorted(rows, key=lambda r: min(abs(r[0] - t0), abs(r[0] - t1)))[:2]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in inside for n, v in zip(names, r[3][2:6]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": reasons, "samples": len(inside)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_config(wl) -> dict:
+    what = "full pipeline: detector LUT, 2/98 % stretch, uint8 out" if wl.stretch else "detector LUT only, uint16 out"
+    in_bytes = wl.pixels * 2
+    return {"workload": "%s: %d bands x %d x %d uint16, %d-bit, %s" % (wl.name, wl.bands, wl.height, wl.width,
+                                                                      wl.bits, what),
+            "bands": wl.bands, "height": wl.height, "width": wl.width, "bits": wl.bits,
+            "pixels_per_step": wl.pixels,
+            "l2": ("inputs larger than L2 (%.2f GB read per step)" % (in_bytes / 1e9)) if in_bytes > 129e6
+            else "inputs smaller than L2 (%.1f MB); L2 not flushed" % (in_bytes / 1e6)}
+
+
+def gen_inputs(wl, seed_offset: int, raw_out=None):
+    import synth
+    raw = synth.raster(wl.seed + seed_offset, wl.bands, wl.height, wl.width, wl.bits, dead_frac=wl.dead_frac,
+                       sat_frac=wl.sat_frac, out=raw_out)
+    A, G, O = synth.coeff_set(wl.seed + seed_offset, wl.bands, wl.width)
+    return raw, A, G, O
+
+
+# ----------------------------------------------------------------------------- reference arm (the CPU oracle)
+
+def run_reference(args, wl):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    band = synth.scene(wl.seed, 0, wl.height, wl.width, wl.bits, dead_frac=wl.dead_frac, sat_frac=wl.sat_frac)
+    A, G, O = synth.coeffs(wl.seed, 0, wl.width)
+    A, G, O = A[None], G[None], O[None]
+    # size each step so that warm-up + timed steps take about two minutes in all
+    probe_rows = min(wl.height, 256)
+    t = time.perf_counter()
+    oracle.correct_image(band[None, :probe_rows], A, G, O, wl.bits, stretch=wl.stretch)
+    rate = probe_rows * wl.width / max(time.perf_counter() - t, 1e-6)
+    per_step = 120.0 / max(1, args.steps + args.warmup)
+    rows = int(max(1, min(wl.height, per_step * rate / wl.width)))
+    sample = band[None, :rows]
+    for _ in range(args.warmup):
+        oracle.correct_image(sample, A, G, O, wl.bits, stretch=wl.stretch)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.correct_image(sample, A, G, O, wl.bits, stretch=wl.stretch)
+    dt = time.perf_counter() - t
+    px = rows * wl.width
+    value = px * args.steps / dt / 1e9
+    desc = "band 0, rows 0-%d (%d px) of the %s workload per step, single-threaded C oracle" % (rows - 1, px, wl.name)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": workload_config(wl),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- the CUDA path
+
+def run_lutc(args, wl):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+
+    import paper_1505_05655_gb300 as lutc
+    from paper_1505_05655_gb300._lib import LUTC_STRETCH
+
+    lib = lutc.lib()
+    # inputs: generated straight into pinned host memory (the end-to-end leg copies from there)
+    shape = (wl.bands, wl.height, wl.width)
+    raw_h = torch.empty(shape, dtype=torch.uint16, pin_memory=True)
+    _, A, G, O = gen_inputs(wl, rank, raw_out=raw_h.numpy())
+    out_dtype = torch.uint8 if wl.stretch else torch.uint16
+    out_h = torch.empty(shape, dtype=out_dtype, pin_memory=True)
+    raw = raw_h.to(device)
+    dA, dG, dO = (torch.from_numpy(a).to(device) for a in (A, G, O))
+    out = torch.empty(shape, dtype=out_dtype, device=device)
+    desc = lutc.raster_desc(raw, wl.bits)
+    cd = lutc.coeff_descs(dA, dG, dO)
+    wsb = torch.empty(max(256, lutc.correct_image_workspace(desc)), dtype=torch.uint8, device=device)
+    stream = torch.cuda.current_stream(device)
+    st = ctypes.c_void_p(stream.cuda_stream)
+    flags = LUTC_STRETCH if wl.stretch else 0
+    pitch = out.stride(1) * out.element_size()
+    call = lambda: lib.lutc_correct_image(ctypes.byref(desc), cd, flags, ctypes.c_void_p(out.data_ptr()), pitch,
+                                          ctypes.c_void_p(wsb.data_ptr()), wsb.numel(), st)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize(device)
+
+    dev_id = None
+    try:
+        dev_id = str(torch.cuda.get_device_properties(device).uuid)
+        dev_id = dev_id if dev_id.startswith("GPU-") else "GPU-" + dev_id
+    except Exception:
+        dev_id = None
+    sampler = ClockSampler(dev_id)
+
+    for _ in range(max(3, args.warmup)):
+        rc = call()
+        if rc:
+            raise RuntimeError("lutc_correct_image failed: %d" % rc)
+    barrier()
+    if wl.stretch:
+        lutc.trace_enable(args.steps)
+    t_ev0, t_ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    wall0 = time.time()
+    t_ev0.record(stream)
+    for _ in range(args.steps):
+        rc = call()
+        if rc:
+            raise RuntimeError("lutc_correct_image failed: %d" % rc)
+    t_ev1.record(stream)
+    barrier()
+    wall1 = time.time()
+    ms = t_ev0.elapsed_time(t_ev1)
+    phases = lutc.trace_read(args.steps) if wl.stretch else []
+    if wl.stretch:
+        lutc.trace_enable(0)
+    clocks = sampler.stop(wall0, wall1)
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = wl.pixels * ws * args.steps / (ms * 1e-3) / 1e9
+
+    # keep this step's output for the parity check against the oracle below
+    out_h.copy_(out)
+
+    peak, peak_src = peaks()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": workload_config(wl)}
+    bytes_per_px = 5 if wl.stretch else 4
+    line["hbm_frac_step"] = wl.pixels * bytes_per_px / (ms_step * 1e-3) / 1e9 / peak
+    if phases:
+        avg = [statistics.fmean(p[i] for p in phases) for i in range(3)]
+        names = ["k_strip_hist", "k_stretch", "k_strip_apply"]
+        alg = [2 * wl.pixels, 8 * wl.bands * (1 << wl.bits), 3 * wl.pixels]
+        dom = max(range(3), key=lambda i: avg[i])
+        ach = alg[dom] / (avg[dom] * 1e-3) / 1e9
+        line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                            "traffic": ncu_traffic(names[dom], wl.name), "kernel": names[dom],
+                            "peak_source": peak_src + " (copy bandwidth)",
+                            "alg_bytes_per_launch": alg[dom]}
+        line["phases_ms"] = {"pass1_hist": avg[0], "scan": avg[1], "pass2_apply": avg[2],
+                             "pass1_GBs": alg[0] / (avg[0] * 1e-3) / 1e9,
+                             "pass2_GBs": alg[2] / (avg[2] * 1e-3) / 1e9}
+    else:
+        ach = wl.pixels * 4 / (ms_step * 1e-3) / 1e9
+        line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                            "traffic": ncu_traffic("k_strip_apply", wl.name), "kernel": "k_strip_apply",
+                            "peak_source": peak_src + " (copy bandwidth)", "alg_bytes_per_launch": 4 * wl.pixels}
+    line["clocks"] = clocks
+    line["gpu_launches"] = (3 if wl.stretch else 1) * args.steps
+
+    # the plain per-call path with materialised tables, for comparison
+    if wl.stretch and not args.no_plain:
+        line["plain"] = run_plain(lutc, raw, dA, dG, dO, wl, device, stream, steps=max(3, min(args.steps, 20)))
+
+    # end to end: pinned host raster -> device, fused correction, result -> pinned host, every step
+    e2e_steps = max(3, min(args.steps, 10))
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        raw.copy_(raw_h, non_blocking=True)
+        rc = call()
+        if rc:
+            raise RuntimeError("lutc_correct_image failed: %d" % rc)
+        out_h.copy_(out, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    ems = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ems], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ems = float(t.item())
+    line["e2e"] = {"value": wl.pixels * ws * e2e_steps / (ems * 1e-3) / 1e9, "unit": UNIT,
+                   "h2d_bytes_per_step": raw_h.numel() * raw_h.element_size(),
+                   "d2h_bytes_per_step": out_h.numel() * out_h.element_size(), "steps": e2e_steps}
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"], line["parity"] = cpu_baseline(wl, raw_h.numpy(), A, G, O, out_h.numpy())
+    if ws > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_plain(lutc, raw, dA, dG, dO, wl, device, stream, steps):
+    """lutgen -> hist -> stretch -> compose -> apply_u8 as separate calls, tables materialised."""
+    import torch
+    L = 1 << wl.bits
+    lut = torch.empty((wl.bands, wl.width, L), dtype=torch.uint16, device=device)
+    clut = torch.empty((wl.bands, wl.width, L), dtype=torch.uint8, device=device)
+    hist = torch.empty((wl.bands, L), dtype=torch.uint64, device=device)
+    S = torch.empty((wl.bands, L), dtype=torch.uint8, device=device)
+    lohi = torch.empty((wl.bands, 2), dtype=torch.int32, device=device)
+    out = torch.empty(raw.shape, dtype=torch.uint8, device=device)
+
+    def step():
+        for b in range(wl.bands):
+            lutc.lutgen(dA[b], dG[b], dO[b], wl.bits, out=lut[b], stream=stream)
+        lutc.hist(raw, dA, dG, dO, wl.bits, out=hist, stream=stream)
+        lutc.stretch(hist, wl.bits, S=S, lohi=lohi, stream=stream)
+        for b in range(wl.bands):
+            lutc.compose(lut[b], S[b], wl.bits, out=clut[b], stream=stream)
+        lutc.apply_u8(raw, clut, wl.bits, out=out, stream=stream)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    ms = e0.elapsed_time(e1) / steps
+    return {"value": wl.pixels / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "path": "lutgen, hist, stretch, compose, apply_u8 as separate calls (%d launches)" % (2 * wl.bands + 3)}
+
+
+def cpu_baseline(wl, raw, A, G, O, gpu_out):
+    """The oracle, single-threaded, on the same host raster; also checks the GPU result bit for bit."""
+    import oracle
+    t = time.perf_counter()
+    ref = oracle.correct_image(raw, A, G, O, wl.bits, stretch=wl.stretch)
+    dt = time.perf_counter() - t
+    base = {"value": wl.pixels / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "the whole %s workload (%d px), single-threaded C oracle, %.1f s" % (wl.name, wl.pixels, dt)}
+    same = bool(np.array_equal(ref, gpu_out))
+    return base, {"bit_exact_vs_oracle": same, "pixels_compared": int(ref.size)}
+
+
+def main():
+    import synth
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="lutc", choices=["lutc", "reference"])
+    ap.add_argument("--workload", default="scene", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    wl = synth.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_lutc(args, wl)
+
+
+if __name__ == "__main__":
+    main()

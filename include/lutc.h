@@ -1,0 +1,204 @@
+/*
+ * lutc -- detector LUT generation and LUT-based image correction on GB300
+ * (sm_103a), behind a plain C ABI.
+ *
+ * The paper's framework (Sections I-II) lets a client name a processing task,
+ * hand over an input data set with a comma-separated parameter list (matrix
+ * dimensions, data type, polynomial orders) and name where the results go;
+ * "LUT generation and image correction" is one of the tasks it names
+ * (Section I).  Each entry point below is one such task on device memory: the
+ * caller passes the input, the parameters and the output, the library runs
+ * its own CUDA kernels on the caller's stream.
+ *
+ * The paper prints no formula for the task; the library defines it as follows
+ * (M = 2^bits - 1, all arithmetic exact on integers, so every output is
+ * bit-exact):
+ *   (L) D[c][x] = clamp(floor((A[c] x^2 + G[c] x + O[c] + 2^15) / 2^16), 0, M)
+ *       per detector (column) c, Q16 quadratic A, gain G, offset O -- the
+ *       polynomial detector model whose coefficients the paper's
+ *       least-squares fit produces (Section III-B).
+ *   (P) corrected pixel d = D[c][min(raw, M)].
+ *   (H) h[v] = number of pixels of a band with corrected value v (2^bits bins).
+ *   (S) N = sum h; lo / hi = least v with 100 cdf(v) >= 2N / >= 98N;
+ *       S[v] = 0 if hi == lo, else clamp(trunc(((v-lo) 255 + trunc((hi-lo)/2)) / (hi-lo)), 0, 255).
+ *   (C) C[c][x] = S[D[c][x]].
+ *   (A) out8 = C[c][min(raw, M)].
+ *
+ * Conventions shared by every call:
+ *   - Pointers to pixels, tables, histograms and workspaces are DEVICE
+ *     pointers owned by the caller; the library never allocates, frees or
+ *     keeps them.  Descriptor structs (lutc_raster, lutc_coeffs arrays) are
+ *     HOST memory, read during the call only.
+ *   - Rasters are planar and band-sequential: band b, row y starts at byte
+ *     b * height * pitch_bytes + y * pitch_bytes of `data`; pixels are uint16.
+ *     Outputs use the same layout with their own row pitch.
+ *   - Tables are [band][column][2^bits] (or [column][2^bits] for one band).
+ *   - bits is 8..16; bands is 1..LUTC_MAX_BANDS.
+ *   - Calls are asynchronous on `stream` (NULL = legacy default stream) and
+ *     return a status: LUTC_OK, or a negative code from argument checks
+ *     (detected before anything is enqueued) or from a failed kernel launch
+ *     (LUTC_ECUDA).  No call throws, exits or aborts the process.
+ */
+#ifndef LUTC_H_
+#define LUTC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LUTC_API __attribute__((visibility("default")))
+#else
+#define LUTC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/** A cudaStream_t; NULL means the legacy default stream. */
+typedef struct CUstream_st* lutc_stream;
+
+/** Status codes. */
+enum {
+    LUTC_OK = 0,
+    LUTC_EINVAL = -1,       /**< an argument is out of range or a pointer is NULL */
+    LUTC_EUNSUPPORTED = -2, /**< valid in principle, not supported by this build */
+    LUTC_ENOMEM = -3,       /**< a workspace is too small / device memory exhausted */
+    LUTC_ECUDA = -4,        /**< a CUDA call or kernel launch failed */
+    LUTC_ETIMEOUT = -5,     /**< a bounded wait expired */
+    LUTC_EBUSY = -6,        /**< admission refused (resource budget) */
+    LUTC_ESHUTDOWN = -7     /**< the object is shutting down */
+};
+
+#define LUTC_MIN_BITS 8
+#define LUTC_MAX_BITS 16
+#define LUTC_MAX_BANDS 64
+
+/** Flags of lutc_correct_image. */
+#define LUTC_STRETCH 1 /**< full pipeline, uint8 output; without it: detector only, uint16 output */
+
+/** Q16 coefficients of one band: A (quadratic), G (gain), O (offset), each int32[ncols], device memory. */
+typedef struct {
+    const int32_t* A;
+    const int32_t* G;
+    const int32_t* O;
+    int32_t ncols;
+} lutc_coeffs;
+
+/** A planar uint16 raster in device memory (layout in the file comment). */
+typedef struct {
+    const uint16_t* data;
+    int64_t pitch_bytes; /**< >= 2 * width; the fast path wants data and pitch 16-byte aligned */
+    int32_t width;       /**< columns (detectors), >= 0 */
+    int32_t height;      /**< rows (scan lines), >= 0 */
+    int32_t bands;       /**< 1..LUTC_MAX_BANDS */
+    int32_t bits;        /**< DN bit depth, 8..16 */
+} lutc_raster;
+
+/** Library version, major * 10000 + minor * 100 + patch. */
+LUTC_API int lutc_version(void);
+
+/** Static, human-readable text of a status code. */
+LUTC_API const char* lutc_strerror(int status);
+
+/**
+ * Step (L), Section I's "LUT generation": lut[c][x] = D[c][x] for c < ncols,
+ * x < 2^bits.  lut: device uint16[ncols][2^bits], written in full.
+ */
+LUTC_API int lutc_lutgen(const lutc_coeffs* coeffs, int bits, uint16_t* lut, lutc_stream stream);
+
+/**
+ * Step (P), Section I's "image correction" with a materialised LUT:
+ * out[b][y][c] = lut[b][c][min(in[b][y][c], M)].
+ * lut: device uint16[bands][width][2^bits]; out: device uint16 rows of out_pitch_bytes (>= 2 * width).
+ */
+LUTC_API int lutc_apply_u16(const lutc_raster* in, const uint16_t* lut, uint16_t* out, int64_t out_pitch_bytes,
+                   lutc_stream stream);
+
+/**
+ * Step (H) with D evaluated from the coefficients: hist[b][v] for every band.
+ * per_band: host array of in->bands coefficient sets (ncols == width).
+ * hist: device uint64[bands][2^bits]; it is zeroed by the call, then filled.
+ */
+LUTC_API int lutc_hist(const lutc_raster* in, const lutc_coeffs* per_band, uint64_t* hist, lutc_stream stream);
+
+/**
+ * Step (S) for `bands` histograms: S[b][v] (device uint8[bands][2^bits]) and
+ * lohi[b] = {lo, hi} (device int32[bands][2]).  N is the histogram's own sum.
+ */
+LUTC_API int lutc_stretch(const uint64_t* hist, int bands, int bits, uint8_t* S, int32_t* lohi, lutc_stream stream);
+
+/**
+ * Step (C) for one band: clut[c][x] = S[min(lut[c][x], M)].
+ * lut: device uint16[ncols][2^bits]; S: device uint8[2^bits]; clut: device uint8[ncols][2^bits].
+ */
+LUTC_API int lutc_compose(const uint16_t* lut, const uint8_t* S, int ncols, int bits, uint8_t* clut, lutc_stream stream);
+
+/**
+ * Step (A) with a materialised composed LUT: out[b][y][c] = clut[b][c][min(in[b][y][c], M)].
+ * clut: device uint8[bands][width][2^bits]; out: device uint8 rows of out_pitch_bytes (>= width).
+ */
+LUTC_API int lutc_apply_u8(const lutc_raster* in, const uint8_t* clut, uint8_t* out, int64_t out_pitch_bytes,
+                  lutc_stream stream);
+
+/** Bytes of workspace lutc_correct_image needs for this raster (0 if the raster is invalid). */
+LUTC_API size_t lutc_correct_image_workspace(const lutc_raster* in);
+
+/**
+ * Byte offsets, inside that workspace, of the per-band tables the fused call
+ * leaves behind: hist (uint64[bands][2^bits]), S (uint8[bands][2^bits]) and
+ * lohi (int32[bands][2]).  Any output pointer may be NULL.  Returns LUTC_OK or LUTC_EINVAL.
+ */
+LUTC_API int lutc_correct_image_tables(const lutc_raster* in, size_t* hist_offset, size_t* S_offset, size_t* lohi_offset);
+
+/**
+ * The whole correction of a raster without materialising any LUT, Section I's
+ * "LUT generation and image correction" as one task.
+ * With LUTC_STRETCH: pass 1 evaluates D on chip and builds every band's
+ * histogram (H), a scan builds S and lo/hi (S), pass 2 re-reads the raw
+ * raster and writes out8 = S[D[c][raw]] (= steps C and A fused); out is
+ * uint8.  Without it: one pass writes the uint16 detector-corrected raster
+ * (P); out is uint16.
+ * per_band: host array of in->bands coefficient sets (ncols == width).
+ * workspace: device memory of at least lutc_correct_image_workspace(in)
+ * bytes, 256-byte aligned, owned by the caller; it must not be shared with
+ * another call in flight.  out_pitch_bytes >= width * sizeof(output element).
+ */
+LUTC_API int lutc_correct_image(const lutc_raster* in, const lutc_coeffs* per_band, int flags, void* out,
+                       int64_t out_pitch_bytes, void* workspace, size_t workspace_bytes, lutc_stream stream);
+
+/**
+ * Pass 2 of the fused correction on its own (steps C and A without a
+ * composed table): out8[b][y][c] = S[b][D[b][c][min(raw, M)]], with D
+ * evaluated from the coefficients.  For callers that build S themselves, e.g.
+ * from histograms summed over several devices before the scan.
+ * S: device uint8[bands][2^bits], 16-byte aligned; out rows of out_pitch_bytes (>= width).
+ */
+LUTC_API int lutc_apply_stretch(const lutc_raster* in, const lutc_coeffs* per_band, const uint8_t* S, uint8_t* out,
+                                int64_t out_pitch_bytes, lutc_stream stream);
+
+/** Phases lutc_trace_read reports per traced call. */
+#define LUTC_TRACE_PHASES 3 /**< pass 1 (histogram clear + histogram), scan, pass 2 */
+
+/**
+ * Tracing of lutc_correct_image (with LUTC_STRETCH): while enabled, each call
+ * records a CUDA event on its stream before pass 1 and after each phase, for
+ * up to `capacity` calls.  capacity 0 disables tracing and releases the
+ * events.  Process-wide; not for concurrent callers.  Returns LUTC_OK,
+ * LUTC_EINVAL or LUTC_ECUDA.
+ */
+LUTC_API int lutc_trace_enable(int capacity);
+
+/**
+ * Waits for the recorded events and writes the phase durations in
+ * milliseconds, ms[call * LUTC_TRACE_PHASES + phase], for at most max_calls
+ * traced calls; then starts a new trace.  Returns the number of calls
+ * written (>= 0) or a negative status.
+ */
+LUTC_API int lutc_trace_read(float* ms, int max_calls);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LUTC_H_ */

@@ -149,7 +149,7 @@ def correct_image(raster: np.ndarray, A, G, O, bits: int, stretch: bool = True, 
     assert raster.ndim == 3 and raster.strides[2] == 2
     bands, h, w = raster.shape
     pitch = raster.strides[1] // 2
-    assert raster.strides[0] == h * raster.strides[1], "bands must be stacked at height * pitch"
+    assert bands == 1 or raster.strides[0] == h * raster.strides[1], "bands must be stacked at height * pitch"
     A = np.ascontiguousarray(_c(A, np.int32)).reshape(bands, w)
     G = np.ascontiguousarray(_c(G, np.int32)).reshape(bands, w)
     O = np.ascontiguousarray(_c(O, np.int32)).reshape(bands, w)

@@ -1,0 +1,217 @@
+"""lutc: detector LUT generation and LUT-based image correction on GB300 (sm_103a).
+
+Python face of the C ABI declared in ``include/lutc.h``.  Each function
+mirrors one entry point of the same name (without the ``lutc_`` prefix) and
+only marshals arguments: rasters are CUDA ``torch.uint16`` tensors
+``[bands, height, width]`` (rows contiguous, bands stacked at height * row
+pitch), coefficients are CUDA ``torch.int32`` tensors ``[bands, width]``,
+tables are CUDA tensors of the dtypes the header states.  Work is enqueued
+on ``stream`` (default: torch's current stream).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from ._lib import (LUTC_MAX_BANDS, LUTC_STRETCH, Coeffs, LutcError, Raster, check, lib)
+
+__all__ = ["LutcError", "lib", "version", "lutgen", "apply_u16", "hist", "stretch", "compose", "apply_u8",
+           "correct_image_workspace", "correct_image_tables", "correct_image", "apply_stretch", "trace_enable",
+           "trace_read", "raster_desc", "coeff_descs"]
+
+
+def _stream(stream, dev):
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _need(t: torch.Tensor, dtype, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype:
+        raise TypeError("%s must be a CUDA %s tensor" % (name, dtype))
+
+
+def version() -> int:
+    return lib().lutc_version()
+
+
+def raster_desc(raw: torch.Tensor, bits: int) -> Raster:
+    """lutc_raster of a ``[bands, H, W]`` (or ``[H, W]``) uint16 CUDA tensor."""
+    _need(raw, torch.uint16, "raw")
+    if raw.dim() == 2:
+        raw = raw.unsqueeze(0)
+    if raw.dim() != 3 or raw.stride(2) != 1:
+        raise ValueError("raw must be [bands, height, width] with contiguous rows")
+    bands, h, w = raw.shape
+    if bands > 1 and raw.stride(0) != h * raw.stride(1):
+        raise ValueError("bands must be stacked at height * row pitch")
+    return Raster(raw.data_ptr(), raw.stride(1) * 2, w, h, bands, bits)
+
+
+def coeff_descs(A: torch.Tensor, G: torch.Tensor, O: torch.Tensor):
+    """Host array of lutc_coeffs, one per band, for ``[bands, W]`` int32 CUDA tensors."""
+    for t, n in ((A, "A"), (G, "G"), (O, "O")):
+        _need(t, torch.int32, n)
+    if A.dim() == 1:
+        A, G, O = A.unsqueeze(0), G.unsqueeze(0), O.unsqueeze(0)
+    bands, w = A.shape
+    arr = (Coeffs * bands)()
+    for b in range(bands):
+        for t in (A[b], G[b], O[b]):
+            if not t.is_contiguous():
+                raise ValueError("coefficient rows must be contiguous")
+        arr[b] = Coeffs(A[b].data_ptr(), G[b].data_ptr(), O[b].data_ptr(), w)
+    return arr
+
+
+def lutgen(A: torch.Tensor, G: torch.Tensor, O: torch.Tensor, bits: int, out: torch.Tensor | None = None,
+           stream=None) -> torch.Tensor:
+    """Detector LUT ``[ncols, 2^bits]`` uint16 of one band."""
+    desc = coeff_descs(A, G, O)
+    if out is None:
+        out = torch.empty((desc[0].ncols, 1 << bits), dtype=torch.uint16, device=A.device)
+    _need(out, torch.uint16, "out")
+    check(lib().lutc_lutgen(ctypes.byref(desc[0]), bits, out.data_ptr(), _stream(stream, A.device)), "lutc_lutgen")
+    return out
+
+
+def _out_like(raw: torch.Tensor, dtype, out):
+    shape = raw.shape if raw.dim() == 3 else (1, *raw.shape)
+    if out is None:
+        out = torch.empty(shape, dtype=dtype, device=raw.device)
+    _need(out, dtype, "out")
+    o3 = out if out.dim() == 3 else out.unsqueeze(0)
+    if o3.stride(2) != 1 or (o3.shape[0] > 1 and o3.stride(0) != o3.shape[1] * o3.stride(1)):
+        raise ValueError("out must be [bands, height, width] with contiguous rows stacked at height * pitch")
+    return out, o3.stride(1) * out.element_size()
+
+
+def apply_u16(raw: torch.Tensor, lut: torch.Tensor, bits: int, out: torch.Tensor | None = None,
+              stream=None) -> torch.Tensor:
+    """out = lut[b][c][min(raw, M)] with a materialised ``[bands, W, 2^bits]`` uint16 LUT."""
+    desc = raster_desc(raw, bits)
+    _need(lut, torch.uint16, "lut")
+    out, pitch = _out_like(raw, torch.uint16, out)
+    check(lib().lutc_apply_u16(ctypes.byref(desc), lut.data_ptr(), out.data_ptr(), pitch,
+                               _stream(stream, raw.device)), "lutc_apply_u16")
+    return out
+
+
+def hist(raw: torch.Tensor, A: torch.Tensor, G: torch.Tensor, O: torch.Tensor, bits: int,
+         out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Per-band histogram ``[bands, 2^bits]`` uint64 of the detector-corrected raster."""
+    desc = raster_desc(raw, bits)
+    cd = coeff_descs(A, G, O)
+    if out is None:
+        out = torch.empty((desc.bands, 1 << bits), dtype=torch.uint64, device=raw.device)
+    _need(out, torch.uint64, "out")
+    check(lib().lutc_hist(ctypes.byref(desc), cd, out.data_ptr(), _stream(stream, raw.device)), "lutc_hist")
+    return out
+
+
+def stretch(hist_: torch.Tensor, bits: int, S: torch.Tensor | None = None, lohi: torch.Tensor | None = None,
+            stream=None):
+    """(S ``[bands, 2^bits]`` uint8, lohi ``[bands, 2]`` int32) of per-band histograms."""
+    _need(hist_, torch.uint64, "hist")
+    h2 = hist_ if hist_.dim() == 2 else hist_.unsqueeze(0)
+    bands = h2.shape[0]
+    if S is None:
+        S = torch.empty((bands, 1 << bits), dtype=torch.uint8, device=hist_.device)
+    if lohi is None:
+        lohi = torch.empty((bands, 2), dtype=torch.int32, device=hist_.device)
+    check(lib().lutc_stretch(hist_.data_ptr(), bands, bits, S.data_ptr(), lohi.data_ptr(),
+                             _stream(stream, hist_.device)), "lutc_stretch")
+    return S, lohi
+
+
+def compose(lut: torch.Tensor, S: torch.Tensor, bits: int, out: torch.Tensor | None = None,
+            stream=None) -> torch.Tensor:
+    """Composed per-column LUT ``[ncols, 2^bits]`` uint8 of one band."""
+    _need(lut, torch.uint16, "lut")
+    _need(S, torch.uint8, "S")
+    ncols = lut.shape[0]
+    if out is None:
+        out = torch.empty((ncols, 1 << bits), dtype=torch.uint8, device=lut.device)
+    check(lib().lutc_compose(lut.data_ptr(), S.data_ptr(), ncols, bits, out.data_ptr(),
+                             _stream(stream, lut.device)), "lutc_compose")
+    return out
+
+
+def apply_u8(raw: torch.Tensor, clut: torch.Tensor, bits: int, out: torch.Tensor | None = None,
+             stream=None) -> torch.Tensor:
+    """out8 = clut[b][c][min(raw, M)] with a materialised ``[bands, W, 2^bits]`` uint8 table."""
+    desc = raster_desc(raw, bits)
+    _need(clut, torch.uint8, "clut")
+    out, pitch = _out_like(raw, torch.uint8, out)
+    check(lib().lutc_apply_u8(ctypes.byref(desc), clut.data_ptr(), out.data_ptr(), pitch,
+                              _stream(stream, raw.device)), "lutc_apply_u8")
+    return out
+
+
+def correct_image_workspace(desc: Raster) -> int:
+    return int(lib().lutc_correct_image_workspace(ctypes.byref(desc)))
+
+
+def correct_image_tables(desc: Raster):
+    h, s, l = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    check(lib().lutc_correct_image_tables(ctypes.byref(desc), ctypes.byref(h), ctypes.byref(s), ctypes.byref(l)),
+          "lutc_correct_image_tables")
+    return h.value, s.value, l.value
+
+
+def correct_image(raw: torch.Tensor, A: torch.Tensor, G: torch.Tensor, O: torch.Tensor, bits: int,
+                  stretch: bool = True, out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                  stream=None, with_tables: bool = False):
+    """The fused correction (uint8 with ``stretch``, else uint16).
+
+    With ``with_tables`` also returns ``(hist [bands, 2^bits] uint64, S [bands, 2^bits] uint8,
+    lohi [bands, 2] int32)`` as views into the workspace.
+    """
+    desc = raster_desc(raw, bits)
+    cd = coeff_descs(A, G, O)
+    out, pitch = _out_like(raw, torch.uint8 if stretch else torch.uint16, out)
+    need = correct_image_workspace(desc)
+    if workspace is None:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=raw.device)
+    _need(workspace, torch.uint8, "workspace")
+    check(lib().lutc_correct_image(ctypes.byref(desc), cd, LUTC_STRETCH if stretch else 0, out.data_ptr(), pitch,
+                                   workspace.data_ptr(), workspace.numel(), _stream(stream, raw.device)),
+          "lutc_correct_image")
+    if not with_tables:
+        return out
+    ho, so, lo = correct_image_tables(desc)
+    L = 1 << bits
+    bands = desc.bands
+    hist_ = workspace[ho:ho + bands * L * 8].view(torch.uint64).view(bands, L)
+    S = workspace[so:so + bands * L].view(bands, L)
+    lohi = workspace[lo:lo + bands * 8].view(torch.int32).view(bands, 2)
+    return out, (hist_, S, lohi)
+
+
+def apply_stretch(raw: torch.Tensor, A: torch.Tensor, G: torch.Tensor, O: torch.Tensor, bits: int,
+                  S: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Pass 2 alone: out8 = S[b][D[b][c][raw]] for a given ``[bands, 2^bits]`` uint8 S."""
+    desc = raster_desc(raw, bits)
+    cd = coeff_descs(A, G, O)
+    _need(S, torch.uint8, "S")
+    out, pitch = _out_like(raw, torch.uint8, out)
+    check(lib().lutc_apply_stretch(ctypes.byref(desc), cd, S.data_ptr(), out.data_ptr(), pitch,
+                                   _stream(stream, raw.device)), "lutc_apply_stretch")
+    return out
+
+
+def trace_enable(capacity: int) -> None:
+    """Record per-phase CUDA events in the next ``capacity`` fused corrections (0 disables)."""
+    check(lib().lutc_trace_enable(int(capacity)), "lutc_trace_enable")
+
+
+def trace_read(max_calls: int):
+    """Per-call phase durations in ms, ``[[pass1, scan, pass2], ...]``; starts a new trace."""
+    buf = (ctypes.c_float * (3 * max(1, max_calls)))()
+    n = lib().lutc_trace_read(buf, int(max_calls))
+    if n < 0:
+        check(n, "lutc_trace_read")
+    return [[buf[3 * i + p] for p in range(3)] for i in range(n)]

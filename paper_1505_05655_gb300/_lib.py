@@ -1,0 +1,96 @@
+"""ctypes binding of the lutc C ABI (``include/lutc.h``).
+
+Argument marshalling only: every step of the correction runs in the CUDA
+library.  Tensors are torch CUDA tensors; the stream defaults to torch's
+current stream of the tensor's device.  If the compiled library is missing
+(and cannot be built) importing raises; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+LUTC_OK = 0
+LUTC_EINVAL = -1
+LUTC_EUNSUPPORTED = -2
+LUTC_ENOMEM = -3
+LUTC_ECUDA = -4
+LUTC_ETIMEOUT = -5
+LUTC_EBUSY = -6
+LUTC_ESHUTDOWN = -7
+LUTC_STRETCH = 1
+LUTC_MAX_BANDS = 64
+LUTC_TRACE_PHASES = 3
+
+
+class LutcError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s failed: %s (%d)" % (where, _strerror(status), status))
+
+
+class Coeffs(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("G", ctypes.c_void_p), ("O", ctypes.c_void_p), ("ncols", ctypes.c_int32)]
+
+
+class Raster(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("pitch_bytes", ctypes.c_int64), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("bands", ctypes.c_int32), ("bits", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_SZ = ctypes.c_size_t
+_RP = ctypes.POINTER(Raster)
+_CP = ctypes.POINTER(Coeffs)
+
+#: name -> (restype, argtypes) for every entry point declared in include/lutc.h
+SIGNATURES = {
+    "lutc_version": (_I, []),
+    "lutc_strerror": (ctypes.c_char_p, [_I]),
+    "lutc_lutgen": (_I, [_CP, _I, _P, _P]),
+    "lutc_apply_u16": (_I, [_RP, _P, _P, _I64, _P]),
+    "lutc_hist": (_I, [_RP, _CP, _P, _P]),
+    "lutc_stretch": (_I, [_P, _I, _I, _P, _P, _P]),
+    "lutc_compose": (_I, [_P, _P, _I, _I, _P, _P]),
+    "lutc_apply_u8": (_I, [_RP, _P, _P, _I64, _P]),
+    "lutc_correct_image_workspace": (_SZ, [_RP]),
+    "lutc_correct_image_tables": (_I, [_RP, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
+    "lutc_correct_image": (_I, [_RP, _CP, _I, _P, _I64, _P, _SZ, _P]),
+    "lutc_apply_stretch": (_I, [_RP, _CP, _P, _P, _I64, _P]),
+    "lutc_trace_enable": (_I, [_I]),
+    "lutc_trace_read": (_I, [ctypes.POINTER(ctypes.c_float), _I]),
+}
+
+_lib = None
+
+
+def lib(build_if_stale: bool = True) -> ctypes.CDLL:
+    """The loaded ``liblutc.so`` (built first if it is missing or older than its sources)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build_if_stale else _build.LIB
+        if not os.path.exists(path):
+            raise ImportError("lutc CUDA library not built: %s" % path)
+        handle = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def _strerror(status: int) -> str:
+    try:
+        return lib().lutc_strerror(status).decode()
+    except Exception:  # pragma: no cover - only while the library is unusable
+        return "status %d" % status
+
+
+def check(status: int, where: str) -> None:
+    if status != LUTC_OK:
+        raise LutcError(status, where)

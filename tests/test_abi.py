@@ -1,0 +1,111 @@
+"""The C-ABI library loads and exports every entry point include/lutc.h declares (CPU only).
+
+Only host-side behaviour is exercised here: symbol export, the status text,
+the workspace size query and argument checks that return before anything
+reaches the GPU.  Nothing here launches a kernel.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1505_05655_gb300 import _lib
+from paper_1505_05655_gb300._lib import Coeffs, Raster
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lutc.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^LUTC_API\s+[\w\s\*]+?\b(lutc_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_path():
+    names = declared_functions()
+    for n in ("lutc_lutgen", "lutc_apply_u16", "lutc_hist", "lutc_stretch", "lutc_compose", "lutc_apply_u8",
+              "lutc_correct_image"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _lib.lib()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, "binding lacks " + name
+
+
+def test_version_and_strerror():
+    lib = _lib.lib()
+    assert lib.lutc_version() >= 10000
+    assert lib.lutc_strerror(0) == b"ok"
+    assert lib.lutc_strerror(-1) == b"invalid argument"
+    assert lib.lutc_strerror(12345) == b"unknown status"
+
+
+def _raster(**kw):
+    r = dict(data=0x10000, pitch_bytes=2 * 100, width=100, height=10, bands=1, bits=12)
+    r.update(kw)
+    return Raster(r["data"], r["pitch_bytes"], r["width"], r["height"], r["bands"], r["bits"])
+
+
+def test_workspace_size_query():
+    lib = _lib.lib()
+    r = _raster(bands=4, bits=12)
+    ws = lib.lutc_correct_image_workspace(ctypes.byref(r))
+    # uint64 histogram + uint8 stretch table per band + lo/hi, 256-byte aligned blocks
+    assert ws >= 4 * 4096 * 8 + 4 * 4096 + 4 * 8 and ws % 256 == 0
+    assert lib.lutc_correct_image_workspace(ctypes.byref(_raster(bits=17))) == 0
+    h, s, l = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    assert lib.lutc_correct_image_tables(ctypes.byref(r), ctypes.byref(h), ctypes.byref(s), ctypes.byref(l)) == 0
+    assert h.value == 0 and s.value >= 4 * 4096 * 8 and l.value >= s.value + 4 * 4096
+
+
+@pytest.mark.parametrize("kw", [dict(bits=7), dict(bits=17), dict(bands=0), dict(bands=65), dict(width=-1),
+                                dict(pitch_bytes=198), dict(data=0), dict(data=0x10001), dict(pitch_bytes=201)])
+def test_bad_raster_is_rejected_before_launch(kw):
+    lib = _lib.lib()
+    r = _raster(**kw)
+    c = (Coeffs * max(1, r.bands))()
+    for i in range(len(c)):
+        c[i] = Coeffs(0x20000, 0x30000, 0x40000, r.width)
+    assert lib.lutc_correct_image(ctypes.byref(r), c, 1, ctypes.c_void_p(0x50000), 100, ctypes.c_void_p(0x60000),
+                                  1 << 20, None) == _lib.LUTC_EINVAL
+    assert lib.lutc_hist(ctypes.byref(r), c, ctypes.c_void_p(0x70000), None) == _lib.LUTC_EINVAL
+
+
+def test_bad_arguments_are_rejected_before_launch():
+    lib = _lib.lib()
+    r = _raster()
+    good = (Coeffs * 1)(Coeffs(0x20000, 0x30000, 0x40000, 100))
+    wrong_cols = (Coeffs * 1)(Coeffs(0x20000, 0x30000, 0x40000, 99))
+    null_coef = (Coeffs * 1)(Coeffs(0, 0x30000, 0x40000, 100))
+    E = _lib.LUTC_EINVAL
+    assert lib.lutc_correct_image(ctypes.byref(r), wrong_cols, 1, ctypes.c_void_p(0x50000), 100, ctypes.c_void_p(0x60000), 1 << 20, None) == E
+    assert lib.lutc_correct_image(ctypes.byref(r), null_coef, 1, ctypes.c_void_p(0x50000), 100, ctypes.c_void_p(0x60000), 1 << 20, None) == E
+    assert lib.lutc_correct_image(ctypes.byref(r), good, 4, ctypes.c_void_p(0x50000), 100, ctypes.c_void_p(0x60000), 1 << 20, None) == E
+    assert lib.lutc_correct_image(ctypes.byref(r), good, 1, None, 100, ctypes.c_void_p(0x60000), 1 << 20, None) == E
+    assert lib.lutc_correct_image(ctypes.byref(r), good, 1, ctypes.c_void_p(0x50000), 99, ctypes.c_void_p(0x60000), 1 << 20, None) == E
+    assert lib.lutc_correct_image(ctypes.byref(r), good, 0, ctypes.c_void_p(0x50000), 199, None, 0, None) == E
+    # too small a workspace is reported as such
+    assert lib.lutc_correct_image(ctypes.byref(r), good, 1, ctypes.c_void_p(0x50000), 100, ctypes.c_void_p(0x60000), 64, None) == _lib.LUTC_ENOMEM
+    assert lib.lutc_correct_image(ctypes.byref(r), None, 1, ctypes.c_void_p(0x50000), 100, ctypes.c_void_p(0x60000), 1 << 20, None) == E
+    one = (Coeffs * 1)(Coeffs(0x20000, 0x30000, 0x40000, 10))
+    assert lib.lutc_lutgen(None, 12, ctypes.c_void_p(0x50000), None) == E
+    assert lib.lutc_lutgen(one, 20, ctypes.c_void_p(0x50000), None) == E
+    assert lib.lutc_lutgen(one, 12, ctypes.c_void_p(0x50008), None) == E  # table must be 16-byte aligned
+    assert lib.lutc_stretch(None, 1, 12, ctypes.c_void_p(0x50000), ctypes.c_void_p(0x60000), None) == E
+    assert lib.lutc_stretch(ctypes.c_void_p(0x40000), 0, 12, ctypes.c_void_p(0x50000), ctypes.c_void_p(0x60000), None) == E
+    assert lib.lutc_compose(ctypes.c_void_p(0x40000), None, 10, 12, ctypes.c_void_p(0x60000), None) == E
+    assert lib.lutc_apply_u8(ctypes.byref(r), None, ctypes.c_void_p(0x60000), 100, None) == E
+    assert lib.lutc_apply_u16(ctypes.byref(r), ctypes.c_void_p(0x40000), ctypes.c_void_p(0x60000), 199, None) == E
+
+
+def test_empty_inputs_need_no_device_work():
+    lib = _lib.lib()
+    zero = (Coeffs * 1)(Coeffs(0, 0, 0, 0))
+    assert lib.lutc_lutgen(zero, 12, None, None) == 0
+    assert lib.lutc_compose(None, None, 0, 12, None, None) == 0
+    r = _raster(width=0, data=0)
+    assert lib.lutc_apply_u8(ctypes.byref(r), ctypes.c_void_p(0x40000), ctypes.c_void_p(0x60000), 0, None) == 0
+    assert lib.lutc_correct_image(ctypes.byref(r), zero, 0, None, 0, None, 0, None) == 0
