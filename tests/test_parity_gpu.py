@@ -146,7 +146,7 @@ def test_correct_image(case):
     bands, h, w, bits, dead, sat, pad, off, extreme = case
     raw, A, G, O = make_case(1000 + h + w + bits, bands, h, w, bits, dead=dead, sat=sat, extreme_cols=extreme)
     if h * w > 4:
-        raw[0, h // 2, :3] = [65535, (1 << bits), (1 << bits) - 1]  # DN above M
+        raw[0, h // 2, :3] = [65535, min(65535, 1 << bits), (1 << bits) - 1]  # DN above M
     d_raw = pitched_device_raster(raw, pad, off) if (pad or off) else dev(raw)
     dA, dG, dO = dev(A), dev(G), dev(O)
     out, (hist, S, lohi) = lutc.correct_image(d_raw, dA, dG, dO, bits, stretch=True, with_tables=True)
