@@ -297,6 +297,9 @@ def run_lutc(args, wl):
                             "peak_source": peak_src + " (copy bandwidth)", "alg_bytes_per_launch": 4 * wl.pixels}
     line["clocks"] = clocks
     line["gpu_launches"] = (3 if wl.stretch else 1) * args.steps
+    status = ctypes.c_int(-1)
+    lib.lutc_device_status(ctypes.byref(status), st)
+    line["device_status"] = status.value
 
     # the plain per-call path with materialised tables, for comparison
     if wl.stretch and not args.no_plain:

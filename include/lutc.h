@@ -177,6 +177,44 @@ LUTC_API int lutc_correct_image(const lutc_raster* in, const lutc_coeffs* per_ba
 LUTC_API int lutc_apply_stretch(const lutc_raster* in, const lutc_coeffs* per_band, const uint8_t* S, uint8_t* out,
                                 int64_t out_pitch_bytes, lutc_stream stream);
 
+/**
+ * Reads and clears the current device's status word: 0, or the first error a
+ * kernel of this library recorded on the device (LUTC_ETIMEOUT when a bounded
+ * wait inside a kernel expired; the kernel then returned early and its
+ * output is not valid).  Synchronises `stream`.  Returns LUTC_OK or LUTC_ECUDA.
+ */
+LUTC_API int lutc_device_status(int* status, lutc_stream stream);
+
+/** Kernel families of the fused path (lutc_tuning.path). */
+#define LUTC_PATH_AUTO 0  /**< TMA-staged kernels when the raster allows them, else strip kernels */
+#define LUTC_PATH_TMA 1   /**< TMA-staged persistent kernels (needs 16-byte aligned rows, width >= 256) */
+#define LUTC_PATH_STRIP 2 /**< plain strip kernels with 16-byte vector loads (any alignment) */
+
+/**
+ * Launch configuration of the fused path for one bit depth.  Every field 0
+ * means "choose automatically".  column_threads (64, 128 or 256) sets the
+ * strip width to 8 * column_threads detectors; blocks_per_sm caps the
+ * persistent grid below the occupancy maximum.  Results never depend on
+ * these settings, only speed does.
+ */
+typedef struct {
+    int32_t path;
+    int32_t column_threads;
+    int32_t blocks_per_sm;
+} lutc_tuning;
+
+/**
+ * Sets (tuning != NULL) or resets to automatic (NULL) the process-wide launch
+ * configuration used for rasters of `bits` (8..16) by lutc_hist,
+ * lutc_apply_stretch and lutc_correct_image; an autotuner calls this with the
+ * fastest configuration it measured.  Takes effect for calls made after it
+ * returns.  Returns LUTC_OK or LUTC_EINVAL.
+ */
+LUTC_API int lutc_set_tuning(int bits, const lutc_tuning* tuning);
+
+/** Reads the configuration lutc_set_tuning stored for `bits` (all zero if automatic). */
+LUTC_API int lutc_get_tuning(int bits, lutc_tuning* tuning);
+
 /** Phases lutc_trace_read reports per traced call. */
 #define LUTC_TRACE_PHASES 3 /**< pass 1 (histogram clear + histogram), scan, pass 2 */
 

@@ -18,7 +18,7 @@ from ._lib import (LUTC_MAX_BANDS, LUTC_STRETCH, Coeffs, LutcError, Raster, chec
 
 __all__ = ["LutcError", "lib", "version", "lutgen", "apply_u16", "hist", "stretch", "compose", "apply_u8",
            "correct_image_workspace", "correct_image_tables", "correct_image", "apply_stretch", "trace_enable",
-           "trace_read", "raster_desc", "coeff_descs"]
+           "trace_read", "raster_desc", "coeff_descs", "set_tuning", "reset_tuning", "get_tuning"]
 
 
 def _stream(stream, dev):
@@ -46,7 +46,7 @@ def raster_desc(raw: torch.Tensor, bits: int) -> Raster:
     if raw.dim() != 3 or raw.stride(2) != 1:
         raise ValueError("raw must be [bands, height, width] with contiguous rows")
     bands, h, w = raw.shape
-    if bands > 1 and raw.stride(0) != h * raw.stride(1):
+    if bands > 1 and h > 0 and raw.stride(0) != h * raw.stride(1):
         raise ValueError("bands must be stacked at height * row pitch")
     return Raster(raw.data_ptr(), raw.stride(1) * 2, w, h, bands, bits)
 
@@ -84,7 +84,7 @@ def _out_like(raw: torch.Tensor, dtype, out):
         out = torch.empty(shape, dtype=dtype, device=raw.device)
     _need(out, dtype, "out")
     o3 = out if out.dim() == 3 else out.unsqueeze(0)
-    if o3.stride(2) != 1 or (o3.shape[0] > 1 and o3.stride(0) != o3.shape[1] * o3.stride(1)):
+    if o3.stride(2) != 1 or (o3.shape[0] > 1 and o3.shape[1] > 0 and o3.stride(0) != o3.shape[1] * o3.stride(1)):
         raise ValueError("out must be [bands, height, width] with contiguous rows stacked at height * pitch")
     return out, o3.stride(1) * out.element_size()
 
@@ -215,3 +215,21 @@ def trace_read(max_calls: int):
     if n < 0:
         check(n, "lutc_trace_read")
     return [[buf[3 * i + p] for p in range(3)] for i in range(n)]
+
+
+def set_tuning(bits: int, path: int = 0, column_threads: int = 0, blocks_per_sm: int = 0) -> None:
+    """Process-wide launch configuration for ``bits`` (all zeros = automatic)."""
+    from ._lib import Tuning
+    t = Tuning(path, column_threads, blocks_per_sm)
+    check(lib().lutc_set_tuning(bits, ctypes.byref(t)), "lutc_set_tuning")
+
+
+def reset_tuning(bits: int) -> None:
+    check(lib().lutc_set_tuning(bits, None), "lutc_set_tuning")
+
+
+def get_tuning(bits: int):
+    from ._lib import Tuning
+    t = Tuning()
+    check(lib().lutc_get_tuning(bits, ctypes.byref(t)), "lutc_get_tuning")
+    return (t.path, t.column_threads, t.blocks_per_sm)

@@ -23,6 +23,9 @@ LUTC_ESHUTDOWN = -7
 LUTC_STRETCH = 1
 LUTC_MAX_BANDS = 64
 LUTC_TRACE_PHASES = 3
+LUTC_PATH_AUTO = 0
+LUTC_PATH_TMA = 1
+LUTC_PATH_STRIP = 2
 
 
 class LutcError(RuntimeError):
@@ -33,6 +36,10 @@ class LutcError(RuntimeError):
 
 class Coeffs(ctypes.Structure):
     _fields_ = [("A", ctypes.c_void_p), ("G", ctypes.c_void_p), ("O", ctypes.c_void_p), ("ncols", ctypes.c_int32)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("column_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
 
 
 class Raster(ctypes.Structure):
@@ -62,6 +69,9 @@ SIGNATURES = {
     "lutc_correct_image": (_I, [_RP, _CP, _I, _P, _I64, _P, _SZ, _P]),
     "lutc_apply_stretch": (_I, [_RP, _CP, _P, _P, _I64, _P]),
     "lutc_trace_enable": (_I, [_I]),
+    "lutc_device_status": (_I, [ctypes.POINTER(_I), _P]),
+    "lutc_set_tuning": (_I, [_I, ctypes.POINTER(Tuning)]),
+    "lutc_get_tuning": (_I, [_I, ctypes.POINTER(Tuning)]),
     "lutc_trace_read": (_I, [ctypes.POINTER(ctypes.c_float), _I]),
 }
 

@@ -1,6 +1,8 @@
 // Version, status text and argument checks of the lutc C ABI.
 #include <stdint.h>
 
+#include <mutex>
+
 #include "lutc_internal.cuh"
 
 namespace lutc {
@@ -38,6 +40,17 @@ int sm_count()
     return n;
 }
 
+namespace {
+std::mutex g_tuning_mu;
+lutc_tuning g_tuning[LUTC_MAX_BITS + 1];
+}  // namespace
+
+lutc_tuning tuning_for(int bits)
+{
+    std::lock_guard<std::mutex> lock(g_tuning_mu);
+    return g_tuning[bits];
+}
+
 int cuda_status(cudaError_t e)
 {
     if (e == cudaSuccess) return LUTC_OK;
@@ -47,6 +60,29 @@ int cuda_status(cudaError_t e)
 }  // namespace lutc
 
 extern "C" int lutc_version(void) { return 10000; }
+
+extern "C" int lutc_set_tuning(int bits, const lutc_tuning* t)
+{
+    if (bits < LUTC_MIN_BITS || bits > LUTC_MAX_BITS) return LUTC_EINVAL;
+    lutc_tuning v = {0, 0, 0};
+    if (t) {
+        if (t->path < LUTC_PATH_AUTO || t->path > LUTC_PATH_STRIP) return LUTC_EINVAL;
+        if (t->column_threads != 0 && t->column_threads != 64 && t->column_threads != 128 && t->column_threads != 256)
+            return LUTC_EINVAL;
+        if (t->blocks_per_sm < 0 || t->blocks_per_sm > 32) return LUTC_EINVAL;
+        v = *t;
+    }
+    std::lock_guard<std::mutex> lock(lutc::g_tuning_mu);
+    lutc::g_tuning[bits] = v;
+    return LUTC_OK;
+}
+
+extern "C" int lutc_get_tuning(int bits, lutc_tuning* t)
+{
+    if (!t || bits < LUTC_MIN_BITS || bits > LUTC_MAX_BITS) return LUTC_EINVAL;
+    *t = lutc::tuning_for(bits);
+    return LUTC_OK;
+}
 
 extern "C" const char* lutc_strerror(int status)
 {

@@ -28,6 +28,10 @@
 namespace lutc {
 
 int launch_stretch(const unsigned long long* hist, int bands, int bits, uint8_t* S, int32_t* lohi, cudaStream_t st);
+bool tma_eligible(const lutc_raster* in);
+int tma_hist(const lutc_raster* in, const lutc_coeffs* per_band, unsigned long long* hist, cudaStream_t st);
+int tma_apply(const lutc_raster* in, const lutc_coeffs* per_band, const uint8_t* S, void* out, int64_t out_pitch,
+              bool stretch, cudaStream_t st);
 
 namespace {
 
@@ -227,7 +231,12 @@ struct Plan {
     int T;
 };
 
-int pick_threads(int W) { return W > 1024 ? 256 : (W > 512 ? 128 : 64); }
+int pick_threads(int W, int bits)
+{
+    const int t = tuning_for(bits).column_threads;
+    if (t) return t;
+    return W > 1024 ? 256 : (W > 512 ? 128 : 64);
+}
 
 template <typename K>
 Plan plan_strips(K kernel, int T, size_t smem, const lutc_raster* in, StripArgs& a)
@@ -235,10 +244,13 @@ Plan plan_strips(K kernel, int T, size_t smem, const lutc_raster* in, StripArgs&
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, T, smem) != cudaSuccess || per_sm < 1)
         per_sm = 1;
+    const int cap = tuning_for(in->bits).blocks_per_sm;
+    if (cap > 0 && cap < per_sm) per_sm = cap;
     const int strips = (in->width + 8 * T - 1) / (8 * T);
     const int64_t target = (int64_t)sm_count() * per_sm;
     const int64_t per_band_strip = (int64_t)strips * in->bands;
-    int64_t groups = (target + per_band_strip - 1) / per_band_strip;
+    // whole row groups that fit one wave (at least one per strip and band)
+    int64_t groups = target / per_band_strip;
     if (groups < 1) groups = 1;
     if (groups > in->height) groups = in->height;
     if (groups > 65535) groups = 65535;
@@ -288,7 +300,7 @@ int launch_hist_T(StripArgs& a, const lutc_raster* in, unsigned long long* hist,
 
 int launch_hist(StripArgs& a, const lutc_raster* in, unsigned long long* hist, cudaStream_t st)
 {
-    switch (pick_threads(in->width)) {
+    switch (pick_threads(in->width, in->bits)) {
     case 64: return launch_hist_T<64>(a, in, hist, st);
     case 128: return launch_hist_T<128>(a, in, hist, st);
     default: return launch_hist_T<256>(a, in, hist, st);
@@ -314,7 +326,7 @@ int launch_apply_T(StripArgs& a, const lutc_raster* in, const uint8_t* S, void* 
 template <bool kStretch>
 int launch_apply(StripArgs& a, const lutc_raster* in, const uint8_t* S, void* out, int64_t out_pitch, cudaStream_t st)
 {
-    switch (pick_threads(in->width)) {
+    switch (pick_threads(in->width, in->bits)) {
     case 64: return launch_apply_T<64, kStretch>(a, in, S, out, out_pitch, st);
     case 128: return launch_apply_T<128, kStretch>(a, in, S, out, out_pitch, st);
     default: return launch_apply_T<256, kStretch>(a, in, S, out, out_pitch, st);
@@ -407,6 +419,7 @@ extern "C" int lutc_apply_stretch(const lutc_raster* in, const lutc_coeffs* per_
     if ((rc = check_coeff_set(in, per_band))) return rc;
     if ((int64_t)in->width * in->height == 0) return LUTC_OK;
     if (!S || ((uintptr_t)S % 16) || !out || out_pitch_bytes < in->width) return LUTC_EINVAL;
+    if (tma_eligible(in)) return tma_apply(in, per_band, S, out, out_pitch_bytes, true, (cudaStream_t)stream);
     StripArgs a = make_args(in, per_band);
     return launch_apply<true>(a, in, S, out, out_pitch_bytes, (cudaStream_t)stream);
 }
@@ -438,6 +451,7 @@ extern "C" int lutc_hist(const lutc_raster* in, const lutc_coeffs* per_band, uin
     const size_t L = (size_t)1 << in->bits;
     if ((rc = cuda_status(cudaMemsetAsync(hist, 0, (size_t)in->bands * L * 8, st)))) return rc;
     if ((int64_t)in->width * in->height == 0) return LUTC_OK;
+    if (tma_eligible(in)) return tma_hist(in, per_band, reinterpret_cast<unsigned long long*>(hist), st);
     StripArgs a = make_args(in, per_band);
     return launch_hist(a, in, reinterpret_cast<unsigned long long*>(hist), st);
 }
@@ -454,8 +468,13 @@ extern "C" int lutc_correct_image(const lutc_raster* in, const lutc_coeffs* per_
     const bool empty = (int64_t)in->width * in->height == 0;
     if (!empty && (!out || out_pitch_bytes < elem * in->width || out_pitch_bytes % elem)) return LUTC_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    const bool tma = !empty && tma_eligible(in);
     StripArgs a = make_args(in, per_band);
-    if (!stretch) return empty ? LUTC_OK : launch_apply<false>(a, in, nullptr, out, out_pitch_bytes, st);
+    if (!stretch) {
+        if (empty) return LUTC_OK;
+        if (tma) return tma_apply(in, per_band, nullptr, out, out_pitch_bytes, false, st);
+        return launch_apply<false>(a, in, nullptr, out, out_pitch_bytes, st);
+    }
 
     const Layout l = layout_of(in);
     if (!workspace || workspace_bytes < l.total) return LUTC_ENOMEM;
@@ -468,11 +487,13 @@ extern "C" int lutc_correct_image(const lutc_raster* in, const lutc_coeffs* per_
     cudaEvent_t* tr = trace_slot();
     if (tr) cudaEventRecord(tr[0], st);
     if ((rc = cuda_status(cudaMemsetAsync(hist, 0, (size_t)in->bands * L * 8, st)))) return rc;
-    if (!empty && (rc = launch_hist(a, in, hist, st))) return rc;
+    if (!empty && (rc = tma ? tma_hist(in, per_band, hist, st) : launch_hist(a, in, hist, st))) return rc;
     if (tr) cudaEventRecord(tr[1], st);
     if ((rc = launch_stretch(hist, in->bands, in->bits, S, lohi, st))) return rc;
     if (tr) cudaEventRecord(tr[2], st);
-    if (!empty && (rc = launch_apply<true>(a, in, S, out, out_pitch_bytes, st))) return rc;
+    if (!empty && (rc = tma ? tma_apply(in, per_band, S, out, out_pitch_bytes, true, st)
+                            : launch_apply<true>(a, in, S, out, out_pitch_bytes, st)))
+        return rc;
     if (tr) cudaEventRecord(tr[3], st);
     return LUTC_OK;
 }

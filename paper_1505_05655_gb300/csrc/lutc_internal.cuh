@@ -61,6 +61,7 @@ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 int check_raster(const lutc_raster* r);
 int check_coeff_set(const lutc_raster* r, const lutc_coeffs* per_band);
 int sm_count();
+lutc_tuning tuning_for(int bits);  // the stored configuration (zeros = automatic)
 int cuda_status(cudaError_t e);  // cudaSuccess -> LUTC_OK, else LUTC_ECUDA (and clears the sticky-free error)
 
 }  // namespace lutc

@@ -138,6 +138,9 @@ CASES = [
     (2, 77, 1500, 12, 0, 0, 8, 1, 0),     # base not 16-byte aligned
     (2, 90, 3000, 12, 0, 0, 0, 0, 40),    # columns needing int64
     (4, 64, 520, 14, 0.2, 0.01, 0, 0, 3),
+    (8, 3, 600, 12, 0, 0, 0, 0, 0),       # many band changes per block
+    (3, 1000, 300, 10, 0, 0, 0, 0, 0),    # one narrow strip per band
+    (2, 500, 4100, 12, 0, 0, 8, 0, 0),    # pitched rows, 16-byte aligned
 ]
 
 
@@ -223,6 +226,15 @@ def test_fused_equals_plain_chain_on_device():
     np.testing.assert_array_equal(host(fused), host(plain))
 
 
+def test_no_kernel_recorded_a_device_error():
+    import ctypes
+    raw, A, G, O = make_case(6, 2, 200, 3000, 12)
+    lutc.correct_image(dev(raw), dev(A), dev(G), dev(O), 12)
+    status = ctypes.c_int(-99)
+    rc = lutc.lib().lutc_device_status(ctypes.byref(status), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0 and status.value == 0
+
+
 def test_status_errors_surface_as_exceptions():
     raw = torch.zeros((1, 4, 4), dtype=torch.uint16, device="cuda")
     A = torch.zeros((1, 5), dtype=torch.int32, device="cuda")  # wrong width
@@ -265,3 +277,25 @@ def test_full_size_workload(name):
         np.testing.assert_array_equal(got_lohi[b], rl[0])
         np.testing.assert_array_equal(got_S[b], rS[0])
         np.testing.assert_array_equal(got[b], ref[0])
+
+
+@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("column_threads", [64, 128, 256])
+def test_every_launch_configuration_is_exact(path, column_threads):
+    """Both kernel families and every strip width give the oracle's result (speed is all tuning may change)."""
+    cases = [(3, 130, 2600, 12), (2, 97, 777, 14), (2, 64, 1500, 10)]
+    try:
+        for bands, h, w, bits in cases:
+            lutc.set_tuning(bits, path=path, column_threads=column_threads, blocks_per_sm=2 if path == 1 else 0)
+            raw, A, G, O = make_case(900 + w, bands, h, w, bits, sat=0.001)
+            dr, dA, dG, dO = dev(raw), dev(A), dev(G), dev(O)
+            out, (hist, S, lohi) = lutc.correct_image(dr, dA, dG, dO, bits, with_tables=True)
+            ref, (rh, rS, rl) = oracle.correct_image(raw, A, G, O, bits, with_tables=True)
+            np.testing.assert_array_equal(host(hist), rh)
+            np.testing.assert_array_equal(host(out), ref)
+            np.testing.assert_array_equal(host(lutc.correct_image(dr, dA, dG, dO, bits, stretch=False)),
+                                          oracle.correct_image(raw, A, G, O, bits, stretch=False))
+            np.testing.assert_array_equal(host(lutc.apply_stretch(dr, dA, dG, dO, bits, S)), ref)
+    finally:
+        for bits in (10, 12, 14):
+            lutc.reset_tuning(bits)
