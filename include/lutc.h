@@ -215,6 +215,35 @@ LUTC_API int lutc_set_tuning(int bits, const lutc_tuning* tuning);
 /** Reads the configuration lutc_set_tuning stored for `bits` (all zero if automatic). */
 LUTC_API int lutc_get_tuning(int bits, lutc_tuning* tuning);
 
+/** Size of the fixed device scratch array behind lutc_correct_image_static (1 MiB per GPU). */
+#define LUTC_STATIC_SCRATCH_BYTES (1u << 20)
+
+/**
+ * lutc_correct_image without a caller-provided workspace, for callers that
+ * cannot allocate device memory (no device allocator of their own, an
+ * allocation would stall a latency-bound loop, or their framework owns every
+ * device allocation).  The paper has no counterpart: this is a convenience of
+ * this library, not a step of the method.
+ *
+ * Same arguments, result and errors as lutc_correct_image, minus the
+ * workspace.  The scratch (per-band histogram, stretch table and lo/hi) comes
+ * from one file-scope device array of LUTC_STATIC_SCRATCH_BYTES that every GPU
+ * loading the library holds until the process exits; the call allocates
+ * nothing.  A raster whose tables need more than that
+ * (lutc_correct_image_workspace(in) > LUTC_STATIC_SCRATCH_BYTES, e.g. 4 bands
+ * at 16 bits) is rejected with LUTC_ENOMEM before anything is enqueued.
+ *
+ * The first call on a device looks up the array's device address on the
+ * current device (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture on that device.  Every call on a device shares
+ * the one array, which keeps the previous call's tables (the histogram is
+ * cleared at the start of each call): calls that overlap on the GPU --
+ * concurrent streams, or host threads without ordering -- race on it and give
+ * wrong results.  Serialise them on one stream.
+ */
+LUTC_API int lutc_correct_image_static(const lutc_raster* in, const lutc_coeffs* per_band, int flags, void* out,
+                                       int64_t out_pitch_bytes, lutc_stream stream);
+
 /** Phases lutc_trace_read reports per traced call. */
 #define LUTC_TRACE_PHASES 3 /**< pass 1 (histogram clear + histogram), scan, pass 2 */
 

@@ -68,6 +68,7 @@ SIGNATURES = {
     "lutc_correct_image_tables": (_I, [_RP, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
     "lutc_correct_image": (_I, [_RP, _CP, _I, _P, _I64, _P, _SZ, _P]),
     "lutc_apply_stretch": (_I, [_RP, _CP, _P, _P, _I64, _P]),
+    "lutc_correct_image_static": (_I, [_RP, _CP, _I, _P, _I64, _P]),
     "lutc_trace_enable": (_I, [_I]),
     "lutc_device_status": (_I, [ctypes.POINTER(_I), _P]),
     "lutc_set_tuning": (_I, [_I, ctypes.POINTER(Tuning)]),
