@@ -279,12 +279,14 @@ def run_lutc(args, wl):
     line["hbm_frac_step"] = wl.pixels * bytes_per_px / (ms_step * 1e-3) / 1e9 / peak
     if phases:
         avg = [statistics.fmean(p[i] for p in phases) for i in range(3)]
-        names = ["k_strip_hist", "k_stretch", "k_strip_apply"]
+        tma = wl.width >= 256 and raw.data_ptr() % 16 == 0 and (raw.stride(1) * 2) % 16 == 0
+        names = (["pass1 k_tma_strip<hist>", "scan k_stretch", "pass2 k_tma_strip<apply>"] if tma
+                 else ["pass1 k_strip_hist", "scan k_stretch", "pass2 k_strip_apply"])
         alg = [2 * wl.pixels, 8 * wl.bands * (1 << wl.bits), 3 * wl.pixels]
         dom = max(range(3), key=lambda i: avg[i])
         ach = alg[dom] / (avg[dom] * 1e-3) / 1e9
         line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                            "traffic": ncu_traffic(names[dom], wl.name), "kernel": names[dom],
+                            "traffic": ncu_traffic(names[dom].split()[0], wl.name), "kernel": names[dom],
                             "peak_source": peak_src + " (copy bandwidth)",
                             "alg_bytes_per_launch": alg[dom]}
         line["phases_ms"] = {"pass1_hist": avg[0], "scan": avg[1], "pass2_apply": avg[2],
@@ -293,7 +295,7 @@ def run_lutc(args, wl):
     else:
         ach = wl.pixels * 4 / (ms_step * 1e-3) / 1e9
         line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                            "traffic": ncu_traffic("k_strip_apply", wl.name), "kernel": "k_strip_apply",
+                            "traffic": ncu_traffic("pass2", wl.name), "kernel": "detector-only apply",
                             "peak_source": peak_src + " (copy bandwidth)", "alg_bytes_per_launch": 4 * wl.pixels}
     line["clocks"] = clocks
     line["gpu_launches"] = (3 if wl.stretch else 1) * args.steps
