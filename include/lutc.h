@@ -185,6 +185,77 @@ LUTC_API int lutc_apply_stretch(const lutc_raster* in, const lutc_coeffs* per_ba
  */
 LUTC_API int lutc_device_status(int* status, lutc_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent rasters corrected by one persistent launch per
+ * phase.  The paper's server receives tasks from many clients (Sections I-II);
+ * a batch is a set of such tasks of uneven size, bit depth and band count,
+ * each with its own coefficients, run together so that the GPU stays full.
+ * ------------------------------------------------------------------------ */
+
+/** One image of a batch.  Pointers as in lutc_correct_image; per_band is a
+ *  host array of in.bands coefficient sets that is read by lutc_batch_create
+ *  only.  out is uint8 with LUTC_STRETCH, uint16 without. */
+typedef struct {
+    lutc_raster in;
+    const lutc_coeffs* per_band;
+    void* out;
+    int64_t out_pitch_bytes;
+    int32_t flags;
+} lutc_job;
+
+/** Launch configuration of a batch; every field 0 = choose automatically. */
+typedef struct {
+    int32_t column_threads; /**< 64, 128 or 256: strip width 8 * column_threads for every image */
+    int32_t blocks_per_sm;  /**< cap of resident blocks per SM (0 = occupancy maximum) */
+    int32_t use_graph;      /**< 1: the first lutc_batch_run captures the batch in a CUDA graph, later runs replay it */
+} lutc_batch_config;
+
+/** A prepared batch (host object; its device data lives in the caller's workspace). */
+typedef struct lutc_batch_st* lutc_batch;
+
+/** Workspace bytes a batch of these jobs needs (0 if a job is invalid). */
+LUTC_API size_t lutc_batch_workspace(const lutc_job* jobs, int n);
+
+/**
+ * Validates the jobs, plans the launches and writes the device descriptors
+ * (job table, tensor maps, coefficient pointers) into `workspace` with
+ * copies enqueued on `stream`.  The jobs' rasters, coefficients and outputs
+ * must stay valid until lutc_batch_destroy.  config may be NULL.  Images the
+ * TMA kernels cannot take (unaligned rows, width < 256, 16-bit) are corrected
+ * one by one inside the batch with lutc_correct_image.  Returns LUTC_OK,
+ * LUTC_EINVAL (bad job, *out untouched), LUTC_ENOMEM (workspace too small)
+ * or LUTC_ECUDA.
+ */
+LUTC_API int lutc_batch_create(const lutc_job* jobs, int n, const lutc_batch_config* config, void* workspace,
+                               size_t workspace_bytes, lutc_stream stream, lutc_batch* out);
+
+/**
+ * Enqueues the whole batch on `stream`: one histogram pass, one scan and one
+ * gather pass for all LUTC_STRETCH images, one pass for all detector-only
+ * images, then the images corrected one by one.  With use_graph the first
+ * call captures this sequence in a CUDA graph (on an internal stream; make
+ * that first call before capturing `stream` yourself) and every call
+ * launches the graph.  Results equal lutc_correct_image on each image.
+ */
+LUTC_API int lutc_batch_run(lutc_batch batch, lutc_stream stream);
+
+/** Device pointers of job `job`'s tables after a run (LUTC_STRETCH jobs): hist
+ *  uint64[bands][2^bits], S uint8[bands][2^bits], lohi int32[bands][2]. */
+LUTC_API int lutc_batch_tables(lutc_batch batch, int job, uint64_t** hist, uint8_t** S, int32_t** lohi);
+
+/** Releases the host object and its graph; the workspace is the caller's. */
+LUTC_API int lutc_batch_destroy(lutc_batch batch);
+
+/**
+ * The batch autotuner: times every launch configuration (strip width x
+ * blocks per SM) on these jobs -- `reps` runs each after one warm-up run, CUDA
+ * events on `stream`, which it synchronises -- and writes the fastest to
+ * *best (use_graph set) and its mean time in ms to *best_ms (may be NULL).
+ * The outputs are written by every trial.
+ */
+LUTC_API int lutc_batch_autotune(const lutc_job* jobs, int n, void* workspace, size_t workspace_bytes,
+                                 lutc_stream stream, int reps, lutc_batch_config* best, float* best_ms);
+
 /** Kernel families of the fused path (lutc_tuning.path). */
 #define LUTC_PATH_AUTO 0  /**< TMA-staged kernels when the raster allows them, else strip kernels */
 #define LUTC_PATH_TMA 1   /**< TMA-staged persistent kernels (needs 16-byte aligned rows, width >= 256) */
@@ -248,9 +319,10 @@ LUTC_API int lutc_correct_image_static(const lutc_raster* in, const lutc_coeffs*
 #define LUTC_TRACE_PHASES 3 /**< pass 1 (histogram clear + histogram), scan, pass 2 */
 
 /**
- * Tracing of lutc_correct_image (with LUTC_STRETCH): while enabled, each call
- * records a CUDA event on its stream before pass 1 and after each phase, for
- * up to `capacity` calls.  capacity 0 disables tracing and releases the
+ * Tracing of lutc_correct_image (with LUTC_STRETCH) and of lutc_batch_run
+ * without a graph: while enabled, each call records a CUDA event on its
+ * stream before pass 1 and after each phase, for up to `capacity` calls (a
+ * batch's last phase also covers its detector-only and one-by-one images).  capacity 0 disables tracing and releases the
  * events.  Process-wide; not for concurrent callers.  Returns LUTC_OK,
  * LUTC_EINVAL or LUTC_ECUDA.
  */

@@ -146,10 +146,14 @@ def correct_image(raster: np.ndarray, A, G, O, bits: int, stretch: bool = True, 
     ``with_tables`` also ``(hist [bands, 2^bits], S [bands, 2^bits], lohi [bands, 2])``.
     """
     raster = _c(raster, np.uint16)
-    assert raster.ndim == 3 and raster.strides[2] == 2
+    assert raster.ndim == 3
     bands, h, w = raster.shape
-    pitch = raster.strides[1] // 2
-    assert bands == 1 or raster.strides[0] == h * raster.strides[1], "bands must be stacked at height * pitch"
+    if raster.size == 0:
+        pitch = max(w, 1)  # nothing is read
+    else:
+        assert raster.strides[2] == 2
+        pitch = raster.strides[1] // 2
+        assert bands == 1 or raster.strides[0] == h * raster.strides[1], "bands must be stacked at height * pitch"
     A = np.ascontiguousarray(_c(A, np.int32)).reshape(bands, w)
     G = np.ascontiguousarray(_c(G, np.int32)).reshape(bands, w)
     O = np.ascontiguousarray(_c(O, np.int32)).reshape(bands, w)

@@ -18,7 +18,8 @@ from ._lib import (LUTC_MAX_BANDS, LUTC_STRETCH, Coeffs, LutcError, Raster, chec
 
 __all__ = ["LutcError", "lib", "version", "lutgen", "apply_u16", "hist", "stretch", "compose", "apply_u8",
            "correct_image_workspace", "correct_image_tables", "correct_image", "apply_stretch", "trace_enable",
-           "trace_read", "raster_desc", "coeff_descs", "set_tuning", "reset_tuning", "get_tuning"]
+           "trace_read", "raster_desc", "coeff_descs", "set_tuning", "reset_tuning", "get_tuning", "Batch",
+           "batch_autotune"]
 
 
 def _stream(stream, dev):
@@ -43,9 +44,13 @@ def raster_desc(raw: torch.Tensor, bits: int) -> Raster:
     _need(raw, torch.uint16, "raw")
     if raw.dim() == 2:
         raw = raw.unsqueeze(0)
-    if raw.dim() != 3 or raw.stride(2) != 1:
-        raise ValueError("raw must be [bands, height, width] with contiguous rows")
+    if raw.dim() != 3:
+        raise ValueError("raw must be [bands, height, width]")
     bands, h, w = raw.shape
+    if raw.numel() == 0:
+        return Raster(raw.data_ptr(), 2 * w, w, h, bands, bits)
+    if raw.stride(2) != 1:
+        raise ValueError("raw must be [bands, height, width] with contiguous rows")
     if bands > 1 and h > 0 and raw.stride(0) != h * raw.stride(1):
         raise ValueError("bands must be stacked at height * row pitch")
     return Raster(raw.data_ptr(), raw.stride(1) * 2, w, h, bands, bits)
@@ -84,6 +89,8 @@ def _out_like(raw: torch.Tensor, dtype, out):
         out = torch.empty(shape, dtype=dtype, device=raw.device)
     _need(out, dtype, "out")
     o3 = out if out.dim() == 3 else out.unsqueeze(0)
+    if out.numel() == 0:
+        return out, o3.shape[2] * out.element_size()
     if o3.stride(2) != 1 or (o3.shape[0] > 1 and o3.shape[1] > 0 and o3.stride(0) != o3.shape[1] * o3.stride(1)):
         raise ValueError("out must be [bands, height, width] with contiguous rows stacked at height * pitch")
     return out, o3.stride(1) * out.element_size()
@@ -233,3 +240,87 @@ def get_tuning(bits: int):
     t = Tuning()
     check(lib().lutc_get_tuning(bits, ctypes.byref(t)), "lutc_get_tuning")
     return (t.path, t.column_threads, t.blocks_per_sm)
+
+
+class Batch:
+    """A prepared batch of independent corrections (``lutc_batch_*``).
+
+    ``images`` is a list of ``(raw, A, G, O, bits, out, stretch)`` with CUDA
+    tensors as for :func:`correct_image`.  The tensors must outlive the batch.
+    The workspace is allocated here (torch) and passed to the library.
+    """
+
+    def __init__(self, images, column_threads: int = 0, blocks_per_sm: int = 0, use_graph: bool = True,
+                 stream=None, config=None):
+        from ._lib import BatchConfig, Job
+        self._keep = []
+        n = len(images)
+        self.jobs = (Job * max(1, n))()
+        dev = None
+        for i, (raw, A, G, O, bits, out, stretch) in enumerate(images):
+            desc = raster_desc(raw, bits)
+            cd = coeff_descs(A, G, O)
+            out_t, pitch = _out_like(raw, torch.uint8 if stretch else torch.uint16, out)
+            self._keep.append((cd, raw, A, G, O, out_t))
+            self.jobs[i] = Job(desc, ctypes.cast(cd, ctypes.POINTER(Coeffs)), out_t.data_ptr(), pitch,
+                               LUTC_STRETCH if stretch else 0)
+            dev = raw.device
+        self.n = n
+        self.device = dev if dev is not None else torch.device("cuda")
+        need = int(lib().lutc_batch_workspace(self.jobs, n))
+        if need == 0 and n > 0:
+            raise LutcError(-1, "lutc_batch_workspace")
+        self.workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
+        if config is None:
+            config = BatchConfig(column_threads, blocks_per_sm, 1 if use_graph else 0)
+        self.config = config
+        self._h = ctypes.c_void_p()
+        check(lib().lutc_batch_create(self.jobs, n, ctypes.byref(config), self.workspace.data_ptr(),
+                                      self.workspace.numel(), _stream(stream, self.device), ctypes.byref(self._h)),
+              "lutc_batch_create")
+
+    def run(self, stream=None) -> None:
+        check(lib().lutc_batch_run(self._h, _stream(stream, self.device)), "lutc_batch_run")
+
+    def outputs(self):
+        return [k[5] for k in self._keep]
+
+    def tables(self, i: int, bands: int, bits: int):
+        """(hist [bands, 2^bits] uint64, S [bands, 2^bits] uint8, lohi [bands, 2] int32) of image i, as host arrays."""
+        import numpy as np
+        h, s, l = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        check(lib().lutc_batch_tables(self._h, i, ctypes.byref(h), ctypes.byref(s), ctypes.byref(l)),
+              "lutc_batch_tables")
+        L = 1 << bits
+        base = self.workspace.data_ptr()
+        ws = self.workspace
+        hist_ = ws[h.value - base:h.value - base + bands * L * 8].view(torch.uint64).view(bands, L)
+        S = ws[s.value - base:s.value - base + bands * L].view(bands, L)
+        lohi = ws[l.value - base:l.value - base + bands * 8].view(torch.int32).view(bands, 2)
+        return hist_.cpu().numpy(), S.cpu().numpy(), lohi.cpu().numpy()
+
+    def close(self) -> None:
+        if self._h:
+            lib().lutc_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_autotune(images, reps: int = 3, stream=None):
+    """Times every batch launch configuration on these images; returns (BatchConfig, ms)."""
+    from ._lib import BatchConfig
+    b = Batch(images, use_graph=False, stream=stream)
+    best = BatchConfig()
+    ms = ctypes.c_float()
+    try:
+        check(lib().lutc_batch_autotune(b.jobs, b.n, b.workspace.data_ptr(), b.workspace.numel(),
+                                        _stream(stream, b.device), reps, ctypes.byref(best), ctypes.byref(ms)),
+              "lutc_batch_autotune")
+    finally:
+        b.close()
+    return best, ms.value

@@ -47,6 +47,15 @@ class Raster(ctypes.Structure):
                 ("height", ctypes.c_int32), ("bands", ctypes.c_int32), ("bits", ctypes.c_int32)]
 
 
+class Job(ctypes.Structure):
+    _fields_ = [("in_", Raster), ("per_band", ctypes.POINTER(Coeffs)), ("out", ctypes.c_void_p),
+                ("out_pitch_bytes", ctypes.c_int64), ("flags", ctypes.c_int32)]
+
+
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("column_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _I64 = ctypes.c_int64
@@ -72,6 +81,14 @@ SIGNATURES = {
     "lutc_trace_enable": (_I, [_I]),
     "lutc_device_status": (_I, [ctypes.POINTER(_I), _P]),
     "lutc_set_tuning": (_I, [_I, ctypes.POINTER(Tuning)]),
+    "lutc_batch_workspace": (_SZ, [ctypes.POINTER(Job), _I]),
+    "lutc_batch_create": (_I, [ctypes.POINTER(Job), _I, ctypes.POINTER(BatchConfig), _P, _SZ, _P,
+                               ctypes.POINTER(_P)]),
+    "lutc_batch_run": (_I, [_P, _P]),
+    "lutc_batch_tables": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "lutc_batch_destroy": (_I, [_P]),
+    "lutc_batch_autotune": (_I, [ctypes.POINTER(Job), _I, _P, _SZ, _P, _I, ctypes.POINTER(BatchConfig),
+                                 ctypes.POINTER(ctypes.c_float)]),
     "lutc_get_tuning": (_I, [_I, ctypes.POINTER(Tuning)]),
     "lutc_trace_read": (_I, [ctypes.POINTER(ctypes.c_float), _I]),
 }

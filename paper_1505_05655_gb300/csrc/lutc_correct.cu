@@ -27,7 +27,6 @@
 
 namespace lutc {
 
-int launch_stretch(const unsigned long long* hist, int bands, int bits, uint8_t* S, int32_t* lohi, cudaStream_t st);
 bool tma_eligible(const lutc_raster* in);
 int tma_hist(const lutc_raster* in, const lutc_coeffs* per_band, unsigned long long* hist, cudaStream_t st);
 int tma_apply(const lutc_raster* in, const lutc_coeffs* per_band, const uint8_t* S, void* out, int64_t out_pitch,
@@ -365,14 +364,14 @@ void trace_release()
     g_trace = Trace();
 }
 
+}  // namespace
+
 // events of the next traced call, or nullptr when tracing is off or full
 cudaEvent_t* trace_slot()
 {
     if (g_trace.used >= g_trace.capacity) return nullptr;
     return g_trace.ev + (size_t)(g_trace.used++) * (LUTC_TRACE_PHASES + 1);
 }
-
-}  // namespace
 }  // namespace lutc
 
 using namespace lutc;

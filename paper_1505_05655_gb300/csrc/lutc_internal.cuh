@@ -1,6 +1,7 @@
 // Internal declarations of the lutc CUDA library (sm_103a).  Not part of the C ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -55,6 +56,49 @@ struct BandCoef {
 
 inline int64_t table_len(int bits) { return (int64_t)1 << bits; }
 
+// One image of a TMA-path launch.  For a single-image call it travels in the
+// kernel parameters; a batch keeps an array of them in device memory.
+struct JobDesc {
+    int32_t W, H, bits, bands;
+    int32_t strips, vout;
+    int64_t unit_begin;     // first (band, strip, row) unit of this job in the launch
+    uint8_t* out;
+    int64_t out_pitch;
+    int64_t hist_off;       // uint64 elements: band 0's histogram in the launch's histogram region
+    int64_t S_off;          // bytes: band 0's stretch table in the launch's S region
+    const BandCoef* coef;   // device [bands] (batch launches only)
+};
+
+// Per-band tables of a batched scan.
+struct TableDesc {
+    int64_t hist_off;  // uint64 elements
+    int64_t S_off;     // bytes
+    int64_t lohi_off;  // int32 elements
+    int32_t bits;
+    int32_t pad;
+};
+
+// Device-side description of a batch launch (all arrays in device memory).
+struct BatchLaunch {
+    const JobDesc* jobs;
+    const CUtensorMap* maps;  // one per job, 64-byte aligned
+    int32_t njobs;
+    int32_t max_bits;
+    int64_t units;
+    unsigned long long* hist;
+    const uint8_t* S;
+    uint8_t* S_out;
+};
+
+// TMA path (lutc_tma.cu)
+bool tma_encode(CUtensorMap* map, const lutc_raster* in, int column_threads);
+int tma_box_rows(int column_threads);
+int tma_batch_pass(const BatchLaunch& b, int mode, int column_threads, int blocks_per_sm, cudaStream_t st);
+int launch_stretch(const unsigned long long* hist, int bands, int bits, uint8_t* S, int32_t* lohi, cudaStream_t st);
+int stretch_batch(const TableDesc* tables, int ntables, const unsigned long long* hist, uint8_t* S, int32_t* lohi,
+                  cudaStream_t st);
+enum { kModeHist = 0, kModeHistGlobal = 1, kModeApplyStretch = 2, kModeApplyDetector = 3 };
+
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // returns LUTC_OK or LUTC_EINVAL
@@ -62,6 +106,7 @@ int check_raster(const lutc_raster* r);
 int check_coeff_set(const lutc_raster* r, const lutc_coeffs* per_band);
 int sm_count();
 lutc_tuning tuning_for(int bits);  // the stored configuration (zeros = automatic)
+cudaEvent_t* trace_slot();         // LUTC_TRACE_PHASES + 1 events of the next traced call, or nullptr
 int cuda_status(cudaError_t e);  // cudaSuccess -> LUTC_OK, else LUTC_ECUDA (and clears the sticky-free error)
 
 }  // namespace lutc

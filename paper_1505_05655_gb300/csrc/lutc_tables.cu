@@ -113,14 +113,14 @@ __device__ __forceinline__ unsigned long long warp_incl_scan(unsigned long long 
     return v;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_stretch(const unsigned long long* __restrict__ hist, int bits,
-                                                          uint8_t* __restrict__ S, int32_t* __restrict__ lohi)
+// (S) for one band's histogram h (2^bits bins): writes S (2^bits bytes) and lohi[0..1].
+// Called by all kScanThreads threads of a block.
+__device__ __forceinline__ void stretch_band(const unsigned long long* __restrict__ h, int bits,
+                                             uint8_t* __restrict__ S, int32_t* __restrict__ lohi)
 {
     __shared__ unsigned long long warp_tot[kScanThreads / 32];
     __shared__ int s_lo, s_hi;
     const int L = 1 << bits;
-    const int b = blockIdx.x;
-    const unsigned long long* h = hist + (int64_t)b * L;
     const int per = (L + kScanThreads - 1) / kScanThreads;
     const int v0 = min(L, (int)threadIdx.x * per), v1 = min(L, v0 + per);
 
@@ -154,19 +154,35 @@ __global__ void __launch_bounds__(kScanThreads) k_stretch(const unsigned long lo
     __syncthreads();
     const int lo = s_lo, hi = s_hi;
     if (threadIdx.x == 0) {
-        lohi[2 * b] = lo;
-        lohi[2 * b + 1] = hi;
+        lohi[0] = lo;
+        lohi[1] = hi;
     }
     const int64_t span = (int64_t)hi - lo;
-    uint8_t* Sb = S + (int64_t)b * L;
     for (int v = threadIdx.x; v < L; v += kScanThreads) {
         int64_t s = 0;
         if (span != 0) {
             s = (((int64_t)v - lo) * 255 + span / 2) / span;
             s = s < 0 ? 0 : (s > 255 ? 255 : s);
         }
-        Sb[v] = (uint8_t)s;
+        S[v] = (uint8_t)s;
     }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_stretch(const unsigned long long* __restrict__ hist, int bits,
+                                                          uint8_t* __restrict__ S, int32_t* __restrict__ lohi)
+{
+    const int64_t L = (int64_t)1 << bits;
+    const int b = blockIdx.x;
+    stretch_band(hist + b * L, bits, S + b * L, lohi + 2 * b);
+}
+
+// One block per (image, band) of a batch, each with its own bit depth and table offsets.
+__global__ void __launch_bounds__(kScanThreads) k_stretch_batch(const TableDesc* __restrict__ t,
+                                                                const unsigned long long* __restrict__ hist,
+                                                                uint8_t* __restrict__ S, int32_t* __restrict__ lohi)
+{
+    const TableDesc d = t[blockIdx.x];
+    stretch_band(hist + d.hist_off, d.bits, S + d.S_off, lohi + d.lohi_off);
 }
 
 // ---------------------------------------------------------------------------
@@ -228,6 +244,14 @@ int launch_apply_table(const lutc_raster* in, const OutT* table, void* out, int6
 int launch_stretch(const unsigned long long* hist, int bands, int bits, uint8_t* S, int32_t* lohi, cudaStream_t st)
 {
     k_stretch<<<bands, kScanThreads, 0, st>>>(hist, bits, S, lohi);
+    return cuda_status(cudaGetLastError());
+}
+
+int stretch_batch(const TableDesc* tables, int ntables, const unsigned long long* hist, uint8_t* S, int32_t* lohi,
+                  cudaStream_t st)
+{
+    if (ntables <= 0) return LUTC_OK;
+    k_stretch_batch<<<ntables, kScanThreads, 0, st>>>(tables, hist, S, lohi);
     return cuda_status(cudaGetLastError());
 }
 

@@ -41,8 +41,6 @@
 
 namespace lutc {
 
-int launch_stretch(const unsigned long long* hist, int bands, int bits, uint8_t* S, int32_t* lohi, cudaStream_t st);
-
 namespace {
 
 constexpr int kConsumers = 256;            // consumer threads per block (8 warps)
@@ -54,22 +52,33 @@ constexpr int kTileBytes = kConsumers * 16 * kRowsPerThread;  // 16 KB
 constexpr int kRingBytes = kStages * kTileBytes;
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
 
-enum Mode { kHist = 0, kHistGlobal = 1, kApplyStretch = 2, kApplyDetector = 3 };
+enum Mode { kHist = kModeHist, kHistGlobal = kModeHistGlobal, kApplyStretch = kModeApplyStretch,
+            kApplyDetector = kModeApplyDetector };
 
 __device__ int g_device_status;  // 0, or the first error a kernel of this library recorded
 
+// Single-image launch: everything in the kernel parameters.
 struct TmaArgs {
     CUtensorMap map;  // uint16 [bands * H][W], row stride = pitch, box {256, rows per tile}
-    int W, H, bits, bands;
-    int strips;
+    JobDesc job;
+    BandCoef coef[LUTC_MAX_BANDS];
     int64_t units;
     int64_t units_per_block;
-    uint8_t* out;
-    int64_t out_pitch;
-    int vout;
-    const uint8_t* S;
     unsigned long long* hist;
-    BandCoef coef[LUTC_MAX_BANDS];
+    const uint8_t* S;
+    int32_t max_bits;
+};
+
+// Batch launch: job table, tensor maps and coefficient arrays in device memory.
+struct BatchArgs {
+    const JobDesc* jobs;
+    const CUtensorMap* maps;
+    int32_t njobs;
+    int32_t max_bits;
+    int64_t units;
+    int64_t units_per_block;
+    unsigned long long* hist;
+    const uint8_t* S;
 };
 
 // ---------------------------------------------------------------------------
@@ -161,8 +170,73 @@ __device__ __forceinline__ void unpack_clamped(const uint4 v, uint32_t M2, uint3
     x[6] = w3 & 0xffffu; x[7] = w3 >> 16;
 }
 
-template <int TC, int MODE>
-__global__ void __launch_bounds__(kThreads) k_tma_strip(const __grid_constant__ TmaArgs a)
+// 8 output bytes (lo: bytes 0-3, hi: bytes 4-7) at any address, with the widest aligned stores
+__device__ __forceinline__ void store8(uint8_t* dst, uint32_t lo, uint32_t hi)
+{
+    const uintptr_t a = reinterpret_cast<uintptr_t>(dst);
+    if ((a & 7) == 0) {
+        *reinterpret_cast<uint2*>(dst) = make_uint2(lo, hi);
+    } else if ((a & 3) == 0) {
+        reinterpret_cast<uint32_t*>(dst)[0] = lo;
+        reinterpret_cast<uint32_t*>(dst)[1] = hi;
+    } else if ((a & 1) == 0) {
+        uint16_t* d = reinterpret_cast<uint16_t*>(dst);
+        d[0] = (uint16_t)lo; d[1] = (uint16_t)(lo >> 16);
+        d[2] = (uint16_t)hi; d[3] = (uint16_t)(hi >> 16);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dst[k] = (uint8_t)(lo >> (8 * k));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dst[4 + k] = (uint8_t)(hi >> (8 * k));
+    }
+}
+
+// 8 uint16 outputs at any even address
+__device__ __forceinline__ void store8x16(uint8_t* dst, const uint32_t (&d)[8])
+{
+    const uintptr_t a = reinterpret_cast<uintptr_t>(dst);
+    const uint32_t w0 = d[0] | (d[1] << 16), w1 = d[2] | (d[3] << 16), w2 = d[4] | (d[5] << 16), w3 = d[6] | (d[7] << 16);
+    if ((a & 15) == 0) {
+        *reinterpret_cast<uint4*>(dst) = make_uint4(w0, w1, w2, w3);
+    } else if ((a & 7) == 0) {
+        reinterpret_cast<uint2*>(dst)[0] = make_uint2(w0, w1);
+        reinterpret_cast<uint2*>(dst)[1] = make_uint2(w2, w3);
+    } else if ((a & 3) == 0) {
+        uint32_t* p = reinterpret_cast<uint32_t*>(dst);
+        p[0] = w0; p[1] = w1; p[2] = w2; p[3] = w3;
+    } else {
+        uint16_t* p = reinterpret_cast<uint16_t*>(dst);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) p[k] = (uint16_t)d[k];
+    }
+}
+
+template <bool kBatch, class Args>
+__device__ __forceinline__ JobDesc job_of(const Args& a, int j)
+{
+    if constexpr (kBatch) return a.jobs[j];
+    else return a.job;
+}
+
+template <bool kBatch, class Args>
+__device__ __forceinline__ const CUtensorMap* map_of(const Args& a, int j)
+{
+    if constexpr (kBatch) return a.maps + j;
+    else return &a.map;
+}
+
+template <bool kBatch, class Args>
+__device__ __forceinline__ BandCoef coef_of(const Args& a, const JobDesc& J, int band)
+{
+    if constexpr (kBatch) return J.coef[band];
+    else return a.coef[band];
+}
+
+// One persistent kernel for both passes (MODE) and both launch kinds (kBatch).
+// The launch's work is the concatenation over its jobs of (band, strip, row)
+// units; block k takes units [k q, (k + 1) q) and walks them tile by tile.
+template <int TC, int MODE, bool kBatch, class Args>
+__global__ void __launch_bounds__(kThreads) k_tma_strip(const __grid_constant__ Args a)
 {
     constexpr int SW = 8 * TC;                 // strip width (columns)
     constexpr int P = kConsumers / TC;         // row phases
@@ -179,8 +253,6 @@ __global__ void __launch_bounds__(kThreads) k_tma_strip(const __grid_constant__ 
     uint32_t* hs = reinterpret_cast<uint32_t*>(table);
 
     const int tid = threadIdx.x;
-    const int L = 1 << a.bits;
-    const int32_t M = L - 1;
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -191,18 +263,33 @@ __global__ void __launch_bounds__(kThreads) k_tma_strip(const __grid_constant__ 
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (MODE == kHist)
-        for (int i = tid; i < L; i += kThreads) hs[i] = 0;
+        for (int i = tid; i < (1 << a.max_bits); i += kThreads) hs[i] = 0;
     __syncthreads();
 
-    // This block's share of the (band, strip, row) space, walked without divisions.
+    // This block's share of the units, walked without divisions after the first.
     const int64_t u0 = (int64_t)blockIdx.x * a.units_per_block;
     const int64_t u1 = min(a.units, u0 + a.units_per_block);
     if (u0 >= u1) return;
     int64_t left = u1 - u0;
-    const int64_t seg0 = u0 / a.H;
-    int row = (int)(u0 - seg0 * a.H);
-    int band = (int)(seg0 / a.strips);
-    int strip = (int)(seg0 - (int64_t)band * a.strips);
+    int j = 0;
+    if constexpr (kBatch) {
+        int lo = 0, hi = a.njobs - 1;  // last job whose first unit is <= u0
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.jobs[mid].unit_begin <= u0) lo = mid;
+            else hi = mid - 1;
+        }
+        j = lo;
+    }
+    JobDesc J = job_of<kBatch>(a, j);
+    int row, band, strip;
+    {
+        const int64_t r = u0 - J.unit_begin;
+        const int64_t seg = r / J.H;
+        row = (int)(r - seg * J.H);
+        band = (int)(seg / J.strips);
+        strip = (int)(seg - (int64_t)band * J.strips);
+    }
     int stage = 0;
     uint32_t phase = 0;
 
@@ -212,29 +299,36 @@ __global__ void __launch_bounds__(kThreads) k_tma_strip(const __grid_constant__ 
         int issued = 0;
         bool ok = true;
         while (left > 0) {
-            const int nrows = (int)min((int64_t)min(RT, a.H - row), left);
+            const int nrows = (int)min((int64_t)min(RT, J.H - row), left);
             if (issued >= kStages && !mbar_wait(&empty[stage], phase ^ 1u)) {
                 ok = false;
                 break;
             }
             const int x0 = strip * SW;
-            const int nb = min(NB, (a.W - x0 + 255) >> 8);
+            const int nb = min(NB, (J.W - x0 + 255) >> 8);
             mbar_arrive_expect_tx(&full[stage], (uint32_t)(nb * 512 * RT));
             unsigned char* dst = ring + stage * kTileBytes;
-            const int y = band * a.H + row;
-            for (int b = 0; b < nb; ++b) tma_load_2d(dst + b * (RT * 512), &a.map, &full[stage], x0 + b * 256, y);
+            const int y = band * J.H + row;
+            const CUtensorMap* map = map_of<kBatch>(a, j);
+            for (int b = 0; b < nb; ++b) tma_load_2d(dst + b * (RT * 512), map, &full[stage], x0 + b * 256, y);
             ++issued;
             left -= nrows;
             row += nrows;
-            if (row == a.H) {
+            if (row == J.H) {
                 row = 0;
-                if (++strip == a.strips) { strip = 0; ++band; }
+                if (++strip == J.strips) {
+                    strip = 0;
+                    if (++band == J.bands) {
+                        band = 0;
+                        if (kBatch && left > 0) J = job_of<kBatch>(a, ++j);
+                    }
+                }
             }
             if (++stage == kStages) { stage = 0; phase ^= 1u; }
         }
         if (!ok) {
             // let every copy issued land before the block's shared memory goes away
-            for (int j = 0; j < kStages && j < issued; ++j) {
+            for (int i = 0; i < kStages && i < issued; ++i) {
                 if (--stage < 0) { stage = kStages - 1; phase ^= 1u; }
                 mbar_wait(&full[stage], phase);
             }
@@ -246,23 +340,27 @@ __global__ void __launch_bounds__(kThreads) k_tma_strip(const __grid_constant__ 
     const int ct = tid % TC;  // column thread: owns columns strip * SW + ct * 8 .. + 7
     const int ph = tid / TC;  // row phase
     const int lane = tid & 31;
-    const uint32_t M2 = (uint32_t)M | ((uint32_t)M << 16);
     const unsigned char* my = ring + (ct >> 5) * (RT * 512) + (ct & 31) * 16 + ph * 512;
     uint32_t sync_phase = 0;
     bool new_seg = true;
-    int cur_band = -1;
+    bool have_band = false;
+    int L = 1 << J.bits;
+    int32_t M = L - 1;
+    uint32_t M2 = (uint32_t)M | ((uint32_t)M << 16);
+    unsigned long long* hb = nullptr;  // global histogram of the band being counted
+    int hb_len = 0;
     int32_t A[8], G[8], O[8];
     bool fits = true;
     int n = 0, c0 = 0;
     while (left > 0) {
-        const int nrows = (int)min((int64_t)min(RT, a.H - row), left);
+        const int nrows = (int)min((int64_t)min(RT, J.H - row), left);
         if (new_seg) {
-            if (band != cur_band) {
-                if (MODE == kHist && cur_band >= 0) {
+            if (strip == 0 || !have_band) {
+                // a new band (of this or the next job) starts
+                if (MODE == kHist && have_band) {
                     // every consumer is done with the previous band: flush it and clear
                     if (!consumer_sync(csync, sync_phase)) return;
-                    unsigned long long* hb = a.hist + (int64_t)cur_band * L;
-                    for (int i = tid; i < L; i += kConsumers) {
+                    for (int i = tid; i < hb_len; i += kConsumers) {
                         const uint32_t c = hs[i];
                         if (c) {
                             atomicAdd(hb + i, (unsigned long long)c);
@@ -271,39 +369,46 @@ __global__ void __launch_bounds__(kThreads) k_tma_strip(const __grid_constant__ 
                     }
                     if (!consumer_sync(csync, sync_phase)) return;
                 }
+                L = 1 << J.bits;
+                M = L - 1;
+                M2 = (uint32_t)M | ((uint32_t)M << 16);
+                hb = a.hist + J.hist_off + (int64_t)band * L;
+                hb_len = L;
                 if (MODE == kApplyStretch) {
-                    if (cur_band >= 0 && !consumer_sync(csync, sync_phase)) return;
-                    const uint4* src = reinterpret_cast<const uint4*>(a.S + (int64_t)band * L);
+                    if (have_band && !consumer_sync(csync, sync_phase)) return;
+                    const uint4* src = reinterpret_cast<const uint4*>(a.S + J.S_off + (int64_t)band * L);
                     for (int i = tid; i < L / 16; i += kConsumers) reinterpret_cast<uint4*>(table)[i] = src[i];
                     if (!consumer_sync(csync, sync_phase)) return;
                 }
-                cur_band = band;
+                have_band = true;
             }
             new_seg = false;
             c0 = strip * SW + ct * 8;
-            n = min(8, a.W - c0);
+            n = min(8, J.W - c0);
             fits = true;
-            const BandCoef& cf = a.coef[band];
+            const BandCoef cf = coef_of<kBatch>(a, J, band);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                if (j < n) {
-                    A[j] = __ldg(cf.A + c0 + j);
-                    G[j] = __ldg(cf.G + c0 + j);
-                    O[j] = __ldg(cf.O + c0 + j);
-                    fits = fits && col_fits_i32(A[j], G[j], O[j], M);
+            for (int jj = 0; jj < 8; ++jj) {
+                if (jj < n) {
+                    A[jj] = __ldg(cf.A + c0 + jj);
+                    G[jj] = __ldg(cf.G + c0 + jj);
+                    O[jj] = __ldg(cf.O + c0 + jj);
+                    fits = fits && col_fits_i32(A[jj], G[jj], O[jj], M);
                 } else {
-                    A[j] = 0; G[j] = 0; O[j] = 0;
+                    A[jj] = 0; G[jj] = 0; O[jj] = 0;
                 }
             }
             if (fits) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j) O[j] += 32768;
+                for (int jj = 0; jj < 8; ++jj) O[jj] += 32768;
             }
         }
         if (!mbar_wait(&full[stage], phase)) return;
         const unsigned char* tile = my + stage * kTileBytes;
-        const int64_t orow0 = (int64_t)band * a.H + row + ph;
-        if (n == 8 && fits) {
+        const int64_t orow0 = (int64_t)band * J.H + row + ph;
+        if (fits && n > 0) {
+            // int32-exact columns; a right-edge chunk (n < 8) reads TMA's zero fill past the
+            // edge and masks those pixels out, so it runs at full speed too
 #pragma unroll
             for (int i = 0; i < kRowsPerThread; ++i) {
                 if (ph + i * P < nrows) {
@@ -311,58 +416,66 @@ __global__ void __launch_bounds__(kThreads) k_tma_strip(const __grid_constant__ 
                     uint32_t x[8], d[8];
                     unpack_clamped(v, M2, x);
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) d[j] = det_horner(A[j], G[j], O[j], x[j], M);
+                    for (int jj = 0; jj < 8; ++jj) d[jj] = det_horner(A[jj], G[jj], O[jj], x[jj], M);
                     if (MODE == kHist) {
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) atomicAdd(hs + d[j], 1u);
+                        for (int jj = 0; jj < 8; ++jj)
+                            if (jj < n) atomicAdd(hs + d[jj], 1u);
                     } else if (MODE == kHistGlobal) {
-                        unsigned long long* hb = a.hist + (int64_t)band * L;
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) atomicAdd(hb + d[j], 1ull);
+                        for (int jj = 0; jj < 8; ++jj)
+                            if (jj < n) atomicAdd(hb + d[jj], 1ull);
                     } else if (MODE == kApplyStretch) {
                         uint32_t o[8];
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) o[j] = table[d[j]];
-                        uint8_t* dst = a.out + (orow0 + i * P) * a.out_pitch + c0;
-                        uint2 r;
-                        r.x = o[0] | (o[1] << 8) | (o[2] << 16) | (o[3] << 24);
-                        r.y = o[4] | (o[5] << 8) | (o[6] << 16) | (o[7] << 24);
-                        if (a.vout) {
-                            *reinterpret_cast<uint2*>(dst) = r;
+                        for (int jj = 0; jj < 8; ++jj) o[jj] = table[d[jj]];
+                        uint8_t* dst = J.out + (orow0 + i * P) * J.out_pitch + c0;
+                        const uint32_t lo = o[0] | (o[1] << 8) | (o[2] << 16) | (o[3] << 24);
+                        const uint32_t hi = o[4] | (o[5] << 8) | (o[6] << 16) | (o[7] << 24);
+                        if (n == 8) {
+                            if (J.vout) *reinterpret_cast<uint2*>(dst) = make_uint2(lo, hi);
+                            else store8(dst, lo, hi);
                         } else {
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) dst[j] = (uint8_t)o[j];
+                            for (int jj = 0; jj < 8; ++jj)
+                                if (jj < n) dst[jj] = (uint8_t)o[jj];
                         }
                     } else {
-                        uint8_t* dst = a.out + (orow0 + i * P) * a.out_pitch + (int64_t)c0 * 2;
-                        if (a.vout) {
-                            uint4 r;
-                            r.x = d[0] | (d[1] << 16); r.y = d[2] | (d[3] << 16);
-                            r.z = d[4] | (d[5] << 16); r.w = d[6] | (d[7] << 16);
-                            *reinterpret_cast<uint4*>(dst) = r;
+                        uint8_t* dst = J.out + (orow0 + i * P) * J.out_pitch + (int64_t)c0 * 2;
+                        if (n == 8) {
+                            if (J.vout) {
+                                uint4 r;
+                                r.x = d[0] | (d[1] << 16); r.y = d[2] | (d[3] << 16);
+                                r.z = d[4] | (d[5] << 16); r.w = d[6] | (d[7] << 16);
+                                *reinterpret_cast<uint4*>(dst) = r;
+                            } else {
+                                store8x16(dst, d);
+                            }
                         } else {
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) reinterpret_cast<uint16_t*>(dst)[j] = (uint16_t)d[j];
+                            for (int jj = 0; jj < 8; ++jj)
+                                if (jj < n) reinterpret_cast<uint16_t*>(dst)[jj] = (uint16_t)d[jj];
                         }
                     }
                 }
             }
         } else if (n > 0) {
-            // right-edge chunk or a column that needs int64: exact, slow, few registers
-            const BandCoef& cf = a.coef[band];
+            // a column that needs int64: exact, slow, few registers
+            const BandCoef cf = coef_of<kBatch>(a, J, band);
 #pragma unroll 1
             for (int i = 0; i < kRowsPerThread; ++i) {
                 if (ph + i * P >= nrows) break;
                 const uint16_t* px = reinterpret_cast<const uint16_t*>(tile + i * P * 512);
                 const int64_t orow = orow0 + i * P;
 #pragma unroll 1
-                for (int j = 0; j < n; ++j) {
-                    const uint32_t x = min((uint32_t)px[j], (uint32_t)M);
-                    const uint32_t d = det_i64(__ldg(cf.A + c0 + j), __ldg(cf.G + c0 + j), __ldg(cf.O + c0 + j), x, M);
+                for (int jj = 0; jj < n; ++jj) {
+                    const uint32_t x = min((uint32_t)px[jj], (uint32_t)M);
+                    const uint32_t d =
+                        det_i64(__ldg(cf.A + c0 + jj), __ldg(cf.G + c0 + jj), __ldg(cf.O + c0 + jj), x, M);
                     if (MODE == kHist) atomicAdd(hs + d, 1u);
-                    else if (MODE == kHistGlobal) atomicAdd(a.hist + (int64_t)band * L + d, 1ull);
-                    else if (MODE == kApplyStretch) a.out[orow * a.out_pitch + c0 + j] = table[d];
-                    else reinterpret_cast<uint16_t*>(a.out + orow * a.out_pitch)[c0 + j] = (uint16_t)d;
+                    else if (MODE == kHistGlobal) atomicAdd(hb + d, 1ull);
+                    else if (MODE == kApplyStretch) J.out[orow * J.out_pitch + c0 + jj] = table[d];
+                    else reinterpret_cast<uint16_t*>(J.out + orow * J.out_pitch)[c0 + jj] = (uint16_t)d;
                 }
             }
         }
@@ -370,17 +483,22 @@ __global__ void __launch_bounds__(kThreads) k_tma_strip(const __grid_constant__ 
         if (lane == 0) mbar_arrive(&empty[stage]);
         left -= nrows;
         row += nrows;
-        if (row == a.H) {
+        if (row == J.H) {
             row = 0;
             new_seg = true;
-            if (++strip == a.strips) { strip = 0; ++band; }
+            if (++strip == J.strips) {
+                strip = 0;
+                if (++band == J.bands) {
+                    band = 0;
+                    if (kBatch && left > 0) J = job_of<kBatch>(a, ++j);
+                }
+            }
         }
         if (++stage == kStages) { stage = 0; phase ^= 1u; }
     }
-    if (MODE == kHist && cur_band >= 0) {
+    if (MODE == kHist && have_band) {
         if (!consumer_sync(csync, sync_phase)) return;
-        unsigned long long* hb = a.hist + (int64_t)cur_band * L;
-        for (int i = tid; i < L; i += kConsumers) {
+        for (int i = tid; i < hb_len; i += kConsumers) {
             const uint32_t c = hs[i];
             if (c) atomicAdd(hb + i, (unsigned long long)c);
         }
@@ -413,40 +531,90 @@ int pick_tc(int W, int bits)
     return W >= 4096 ? 256 : (W >= 1024 ? 128 : 64);
 }
 
-template <int TC, int MODE>
-int launch_tc(TmaArgs& a, cudaStream_t st)
+size_t table_bytes(int mode, int max_bits)
 {
-    auto k = k_tma_strip<TC, MODE>;
-    const size_t L = (size_t)1 << a.bits;
-    const size_t table = MODE == kHist ? L * 4 : (MODE == kApplyStretch ? L : 0);
-    const size_t smem = (size_t)kRingBytes + 128 + table;
+    const size_t L = (size_t)1 << max_bits;
+    return mode == kHist ? L * 4 : (mode == kApplyStretch ? L : 0);
+}
+
+// Grid = SMs x resident blocks (capped by blocks_per_sm when > 0), one wave.
+template <class K>
+int grid_for(K k, size_t smem, int blocks_per_sm, int64_t* grid)
+{
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return LUTC_ECUDA;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem) != cudaSuccess || per_sm < 1)
         return LUTC_ECUDA;
+    if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
+    *grid = (int64_t)sm_count() * per_sm;
+    return LUTC_OK;
+}
+
+template <int TC, int MODE>
+int launch_single_tc(TmaArgs& a, cudaStream_t st)
+{
+    auto k = k_tma_strip<TC, MODE, false, TmaArgs>;
+    const size_t smem = (size_t)kRingBytes + 128 + table_bytes(MODE, a.max_bits);
+    int64_t grid = 0;
+    int rc = grid_for(k, smem, tuning_for(a.job.bits).blocks_per_sm, &grid);
+    if (rc) return rc;
     constexpr int SW = 8 * TC;
-    a.strips = (a.W + SW - 1) / SW;
-    a.units = (int64_t)a.bands * a.strips * a.H;
-    const int cap = tuning_for(a.bits).blocks_per_sm;
-    if (cap > 0 && cap < per_sm) per_sm = cap;
-    const int64_t grid = (int64_t)sm_count() * per_sm;
+    a.job.strips = (a.job.W + SW - 1) / SW;
+    a.units = (int64_t)a.job.bands * a.job.strips * a.job.H;
     a.units_per_block = (a.units + grid - 1) / grid;
     k<<<(unsigned)grid, kThreads, smem, st>>>(a);
     return cuda_status(cudaGetLastError());
 }
 
 template <int MODE>
-int launch_mode(TmaArgs& a, cudaStream_t st)
+int launch_single(TmaArgs& a, int tc, cudaStream_t st)
 {
-    switch (pick_tc(a.W, a.bits)) {
-    case 256: return launch_tc<256, MODE>(a, st);
-    case 128: return launch_tc<128, MODE>(a, st);
-    default: return launch_tc<64, MODE>(a, st);
+    switch (tc) {
+    case 256: return launch_single_tc<256, MODE>(a, st);
+    case 128: return launch_single_tc<128, MODE>(a, st);
+    default: return launch_single_tc<64, MODE>(a, st);
+    }
+}
+
+template <int TC, int MODE>
+int launch_batch_tc(BatchArgs& a, int blocks_per_sm, cudaStream_t st)
+{
+    auto k = k_tma_strip<TC, MODE, true, BatchArgs>;
+    const size_t smem = (size_t)kRingBytes + 128 + table_bytes(MODE, a.max_bits);
+    int64_t grid = 0;
+    int rc = grid_for(k, smem, blocks_per_sm, &grid);
+    if (rc) return rc;
+    a.units_per_block = (a.units + grid - 1) / grid;
+    k<<<(unsigned)grid, kThreads, smem, st>>>(a);
+    return cuda_status(cudaGetLastError());
+}
+
+template <int MODE>
+int launch_batch(BatchArgs& a, int tc, int blocks_per_sm, cudaStream_t st)
+{
+    switch (tc) {
+    case 256: return launch_batch_tc<256, MODE>(a, blocks_per_sm, st);
+    case 128: return launch_batch_tc<128, MODE>(a, blocks_per_sm, st);
+    default: return launch_batch_tc<64, MODE>(a, blocks_per_sm, st);
     }
 }
 
 }  // namespace
+
+int tma_box_rows(int column_threads) { return kTileBytes / (16 * column_threads); }
+
+bool tma_encode(CUtensorMap* map, const lutc_raster* in, int column_threads)
+{
+    if (!encode_fn()) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)in->width, (cuuint64_t)in->bands * (cuuint64_t)in->height};
+    const cuuint64_t strides[1] = {(cuuint64_t)in->pitch_bytes};
+    const cuuint32_t box[2] = {256, (cuuint32_t)tma_box_rows(column_threads)};
+    const cuuint32_t estr[2] = {1, 1};
+    return encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<uint16_t*>(in->data), dims, strides, box,
+                       estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                       CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 bool tma_eligible(const lutc_raster* in)
 {
@@ -455,26 +623,24 @@ bool tma_eligible(const lutc_raster* in)
            (int64_t)in->bands * in->height < ((int64_t)1 << 31) && encode_fn() != nullptr;
 }
 
-// Builds the tensor map and the argument block shared by the three passes.
-static int tma_args(const lutc_raster* in, const lutc_coeffs* per_band, TmaArgs& a)
+// Builds the tensor map and the argument block shared by the passes of one image.
+static int tma_args(const lutc_raster* in, const lutc_coeffs* per_band, int tc, TmaArgs& a)
 {
-    const int TC = pick_tc(in->width, in->bits);
-    const int RT = kTileBytes / (16 * TC);  // rows per tile = (kConsumers / TC) * kRowsPerThread
-    const cuuint64_t dims[2] = {(cuuint64_t)in->width, (cuuint64_t)in->bands * (cuuint64_t)in->height};
-    const cuuint64_t strides[1] = {(cuuint64_t)in->pitch_bytes};
-    const cuuint32_t box[2] = {256, (cuuint32_t)RT};
-    const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = encode_fn()(&a.map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<uint16_t*>(in->data), dims,
-                                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return LUTC_ECUDA;
-    a.W = in->width;
-    a.H = in->height;
-    a.bits = in->bits;
-    a.bands = in->bands;
-    a.out = nullptr;
-    a.out_pitch = 0;
-    a.vout = 0;
+    if (!tma_encode(&a.map, in, tc)) return LUTC_ECUDA;
+    JobDesc& J = a.job;
+    J.W = in->width;
+    J.H = in->height;
+    J.bits = in->bits;
+    J.bands = in->bands;
+    J.strips = 0;
+    J.vout = 0;
+    J.unit_begin = 0;
+    J.out = nullptr;
+    J.out_pitch = 0;
+    J.hist_off = 0;
+    J.S_off = 0;
+    J.coef = nullptr;
+    a.max_bits = in->bits;
     a.S = nullptr;
     a.hist = nullptr;
     for (int b = 0; b < LUTC_MAX_BANDS; ++b)
@@ -485,24 +651,46 @@ static int tma_args(const lutc_raster* in, const lutc_coeffs* per_band, TmaArgs&
 int tma_hist(const lutc_raster* in, const lutc_coeffs* per_band, unsigned long long* hist, cudaStream_t st)
 {
     TmaArgs a;
-    int rc = tma_args(in, per_band, a);
+    const int tc = pick_tc(in->width, in->bits);
+    int rc = tma_args(in, per_band, tc, a);
     if (rc) return rc;
     a.hist = hist;
-    return in->bits <= 15 ? launch_mode<kHist>(a, st) : launch_mode<kHistGlobal>(a, st);
+    return in->bits <= 15 ? launch_single<kHist>(a, tc, st) : launch_single<kHistGlobal>(a, tc, st);
 }
 
 int tma_apply(const lutc_raster* in, const lutc_coeffs* per_band, const uint8_t* S, void* out, int64_t out_pitch,
               bool stretch, cudaStream_t st)
 {
     TmaArgs a;
-    int rc = tma_args(in, per_band, a);
+    const int tc = pick_tc(in->width, in->bits);
+    int rc = tma_args(in, per_band, tc, a);
     if (rc) return rc;
-    a.out = reinterpret_cast<uint8_t*>(out);
-    a.out_pitch = out_pitch;
+    a.job.out = reinterpret_cast<uint8_t*>(out);
+    a.job.out_pitch = out_pitch;
     const int64_t vec = stretch ? 8 : 16;
-    a.vout = ((uintptr_t)out % vec == 0) && (out_pitch % vec == 0);
+    a.job.vout = ((uintptr_t)out % vec == 0) && (out_pitch % vec == 0);
     a.S = S;
-    return stretch ? launch_mode<kApplyStretch>(a, st) : launch_mode<kApplyDetector>(a, st);
+    return stretch ? launch_single<kApplyStretch>(a, tc, st) : launch_single<kApplyDetector>(a, tc, st);
+}
+
+int tma_batch_pass(const BatchLaunch& b, int mode, int column_threads, int blocks_per_sm, cudaStream_t st)
+{
+    if (b.units == 0) return LUTC_OK;
+    BatchArgs a;
+    a.jobs = b.jobs;
+    a.maps = b.maps;
+    a.njobs = b.njobs;
+    a.max_bits = b.max_bits;
+    a.units = b.units;
+    a.units_per_block = 0;
+    a.hist = b.hist;
+    a.S = b.S;
+    switch (mode) {
+    case kHist: return launch_batch<kHist>(a, column_threads, blocks_per_sm, st);
+    case kApplyStretch: return launch_batch<kApplyStretch>(a, column_threads, blocks_per_sm, st);
+    case kApplyDetector: return launch_batch<kApplyDetector>(a, column_threads, blocks_per_sm, st);
+    default: return LUTC_EUNSUPPORTED;
+    }
 }
 
 }  // namespace lutc

@@ -144,3 +144,25 @@ BATCH_SEED = 1508
 BATCH_IMAGES = 256
 SERVE_SEED = 1509
 SERVE_SENSORS = 64
+
+
+def batch_image_seed(seed: int, i: int) -> int:
+    """Seed of image i of a batch (each image draws its own scene and coefficients)."""
+    return seed * 1000003 + 7919 * (i + 1)
+
+
+def batch_images(seed: int = BATCH_SEED, n: int = BATCH_IMAGES, nthreads: int = 0, pitch_multiple: int = 8):
+    """The mixed batch: a list of dicts with raw ``[bands, H, pitch]`` uint16 (rows padded to a
+    multiple of ``pitch_multiple`` elements; the image is ``raw[:, :, :width]``), A, G, O
+    ``[bands, width]`` and the image's width, height, bits, bands."""
+    w, h, b, nb = batch_spec(seed, n)
+    out = []
+    for i in range(n):
+        W, H, bits, bands = int(w[i]), int(h[i]), int(b[i]), int(nb[i])
+        pitch = -(-W // pitch_multiple) * pitch_multiple
+        s = batch_image_seed(seed, i)
+        raw = np.zeros((bands, H, pitch), np.uint16)
+        raster(s, bands, H, W, bits, out=raw[:, :, :W], nthreads=nthreads)
+        A, G, O = coeff_set(s, bands, W)
+        out.append(dict(raw=raw, A=A, G=G, O=O, width=W, height=H, bits=bits, bands=bands))
+    return out
