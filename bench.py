@@ -504,6 +504,98 @@ def run_batch(args):
         print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Open-loop Poisson load on the request loop; p50/p99 latency per load and saturation throughput."""
+    import threading
+    import torch
+    import synth
+    import paper_1505_05655_gb300 as lutc
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    nsens = synth.SERVE_SENSORS
+    w, _, bits, bands = synth.batch_spec(synth.SERVE_SEED, nsens)
+    pool_per_sensor = 4
+    server = lutc.Server(budget_bytes=40 << 30, max_batch=32, max_wait_us=2000, streams=3)
+    pool = []  # (sensor, raster on device, output on device, pixels)
+    for sid in range(nsens):
+        W, B, Bt = int(w[sid]), int(bands[sid]), int(bits[sid])
+        A, G, O = synth.coeff_set(synth.batch_image_seed(synth.SERVE_SEED, sid), B, W)
+        server.register_sensor(sid, W, B, Bt, A, G, O)
+        _, hs, _, _ = synth.batch_spec(synth.SERVE_SEED + 1 + sid, pool_per_sensor)
+        for k in range(pool_per_sensor):
+            H = int(hs[k])
+            raw = torch.from_numpy(synth.raster(synth.batch_image_seed(synth.SERVE_SEED + 100 + sid, k), B, H, W,
+                                                Bt)).to(device)
+            out = torch.empty((B, H, W), dtype=torch.uint8, device=device)
+            pool.append((sid, raw, out, B * H * W))
+    rng = np.random.default_rng(synth.SERVE_SEED)
+
+    def drive(rate, n, closed=False):
+        picks = rng.integers(0, len(pool), n)
+        gaps = rng.exponential(1.0 / rate, n) if rate else np.zeros(n)
+        sched = np.cumsum(gaps)
+        tickets = [None] * n
+        infos = [None] * n
+        t0 = time.monotonic() + 0.01
+
+        def submitter():
+            for i in range(n):
+                if not closed:
+                    dt = t0 + sched[i] - time.monotonic()
+                    if dt > 0:
+                        time.sleep(dt)
+                sid, raw, out, _ = pool[picks[i]]
+                while True:
+                    rc, t = server.try_submit(sid, raw, out)
+                    if rc == 0:
+                        break
+                    time.sleep(0.0002)  # queue full under a closed-loop burst
+                tickets[i] = t
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        for i in range(n):
+            while tickets[i] is None:
+                time.sleep(0.0001)
+            infos[i] = server.wait(tickets[i])
+        th.join()
+        lat = np.array([infos[i].done_s - (t0 + sched[i] if not closed else infos[i].submit_s) for i in range(n)])
+        px = sum(pool[j][3] for j in picks)
+        span = max(i.done_s for i in infos) - min(i.submit_s for i in infos)
+        bad = sum(1 for i in infos if i.status != 0)
+        return dict(p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
+                    gpx_s=px / span / 1e9, mean_batch=float(np.mean([i.batch_size for i in infos])),
+                    requests=n, failed=bad, offered_gpx_s=(px / n) * rate / 1e9 if rate else None)
+
+    warm = drive(400, 200)  # first requests of every sensor upload its coefficients
+    loads = {}
+    for rate, n in ((50, max(200, args.steps // 4)), (200, max(400, args.steps)), (800, max(400, 2 * args.steps))):
+        loads[str(rate)] = drive(rate, n)
+    sat = drive(0, max(500, 2 * args.steps), closed=True)
+    # each pool raster's output must equal a single call on it
+    exact = True
+    for sid, raw, out, _ in pool[::9]:
+        b = raw.shape[0]
+        A, G, O = synth.coeff_set(synth.batch_image_seed(synth.SERVE_SEED, sid), b, raw.shape[2])
+        d = lambda a: torch.from_numpy(a).to(device)
+        exact = exact and bool(torch.equal(lutc.correct_image(raw, d(A), d(G), d(O), int(bits[sid])), out))
+    st = server.stats()
+    server.close()
+    line = {"metric": METRIC, "value": sat["gpx_s"], "unit": UNIT, "n_gpus": ws, "steps": sat["requests"],
+            "warmup": warm["requests"], "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "serve: %d sensors from the batch mixture, %d pool rasters each, device-resident; "
+                                   "Poisson arrivals 50/200/800 req/s; budget 40 GiB, batches <= 32 requests or "
+                                   "2 ms, 3 streams" % (nsens, pool_per_sensor),
+                       "l2": "inputs larger than L2 (pool %.1f GB)" % (sum(p_[3] for p_ in pool) * 2 / 1e9)},
+            "latency": loads, "saturation": sat, "warmup_with_cache_misses": warm, "server": st,
+            "outputs_equal_single_calls": exact}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     import synth
     ap = argparse.ArgumentParser()
@@ -511,7 +603,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="lutc", choices=["lutc", "reference"])
-    ap.add_argument("--workload", default="scene", choices=sorted(synth.WORKLOADS) + ["batch"])
+    ap.add_argument("--workload", default="scene", choices=sorted(synth.WORKLOADS) + ["batch", "serve"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--batch-images", type=int, default=256, help="images in the batch workload")
@@ -520,7 +612,10 @@ def main():
     if args.workload == "batch" and args.impl != "reference":
         run_batch(args)
         return
-    wl = synth.WORKLOADS[args.workload if args.workload != "batch" else "scene"]
+    if args.workload == "serve" and args.impl != "reference":
+        run_serve(args)
+        return
+    wl = synth.WORKLOADS[args.workload if args.workload in synth.WORKLOADS else "scene"]
     if args.impl == "reference":
         run_reference(args, wl)
     else:

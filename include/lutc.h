@@ -256,6 +256,82 @@ LUTC_API int lutc_batch_destroy(lutc_batch batch);
 LUTC_API int lutc_batch_autotune(const lutc_job* jobs, int n, void* workspace, size_t workspace_bytes,
                                  lutc_stream stream, int reps, lutc_batch_config* best, float* best_ms);
 
+/* ------------------------------------------------------------------------
+ * Serving: an in-process request loop that plays the paper's GPU server
+ * (Sections I-II: clients submit a task, its data and parameters, and get
+ * the result back).  Requests are queued, admitted against a device-memory
+ * budget, grouped into batches of up to max_batch requests or max_wait_us,
+ * and run as overlapping batches on up to `streams` CUDA streams while new
+ * requests keep arriving (continuous batching).  Each sensor's coefficients
+ * are uploaded to the device on its first request and cached.
+ * ------------------------------------------------------------------------ */
+
+/** Server configuration; zero fields take the defaults in brackets. */
+typedef struct {
+    size_t budget_bytes;  /**< device memory for request buffers and batch tables [40 GiB] */
+    int32_t max_batch;    /**< requests per batch [32] */
+    int32_t max_wait_us;  /**< longest a request waits for its batch to fill [2000]; 1 = launch at once */
+    int32_t streams;      /**< batches in flight [3] */
+    int32_t max_queue;    /**< pending requests before submit returns LUTC_EBUSY [4096] */
+    int32_t fake_device;  /**< test facility: 1 = run no CUDA at all; a batch "completes" fake_latency_us after launch */
+    int32_t fake_latency_us;
+    int32_t fail_every;   /**< test facility: when > 0, every fail_every-th batch is failed on the host with LUTC_ECUDA */
+} lutc_server_config;
+
+/** Request flags. */
+#define LUTC_REQ_HOST 2 /**< raster and output are HOST memory: the server copies them in and out */
+
+/** Per-request outcome, filled by lutc_server_wait. */
+typedef struct {
+    int32_t status;      /**< LUTC_OK, LUTC_ECUDA (failed batch), LUTC_ESHUTDOWN (server closed first) */
+    int32_t batch_size;  /**< requests in the batch that carried it */
+    double submit_s;     /**< host steady-clock seconds at submit */
+    double start_s;      /**< ... when its batch was launched */
+    double done_s;       /**< ... when its batch was seen complete */
+    int32_t cache_miss;  /**< 1 if this request uploaded its sensor's coefficients */
+    int32_t pad;
+} lutc_request_info;
+
+typedef struct lutc_server_st* lutc_server;
+
+/** Creates a server (config may be NULL) on the current device; starts its threads. */
+LUTC_API int lutc_server_create(const lutc_server_config* config, lutc_server* out);
+
+/**
+ * Registers sensor `sensor_id` (0..65535): its raster geometry and host
+ * coefficient arrays A, G, O of [bands][width] int32 (copied).  Nothing is
+ * uploaded until its first request.  Returns LUTC_OK or LUTC_EINVAL.
+ */
+LUTC_API int lutc_server_register_sensor(lutc_server server, int sensor_id, int width, int bands, int bits,
+                                         const int32_t* A, const int32_t* G, const int32_t* O);
+
+/**
+ * Queues one request: the sensor's raster of `height` rows (row pitch
+ * pitch_bytes) is corrected with LUTC_STRETCH into out (row pitch
+ * out_pitch_bytes, uint8).  With LUTC_REQ_HOST in flags both are host
+ * memory; otherwise device memory.  Buffers must stay valid until the ticket
+ * completes.  Returns LUTC_OK and a ticket, LUTC_EINVAL, LUTC_EBUSY (queue
+ * full, or the request alone exceeds the budget) or LUTC_ESHUTDOWN.
+ */
+LUTC_API int lutc_server_submit(lutc_server server, int sensor_id, const uint16_t* raster, int height,
+                                int64_t pitch_bytes, uint8_t* out, int64_t out_pitch_bytes, int flags,
+                                uint64_t* ticket);
+
+/**
+ * Waits up to timeout_us (< 0: forever) for a ticket; on completion fills
+ * *info (may be NULL) and forgets the ticket.  Returns LUTC_OK (see
+ * info->status for the request's own outcome), LUTC_ETIMEOUT (still
+ * running; the ticket stays valid) or LUTC_EINVAL (unknown ticket).
+ */
+LUTC_API int lutc_server_wait(lutc_server server, uint64_t ticket, int64_t timeout_us, lutc_request_info* info);
+
+/** Counters: requests completed, batches launched, bytes of the budget in use now, largest batch. */
+LUTC_API int lutc_server_stats(lutc_server server, uint64_t* completed, uint64_t* batches, size_t* budget_in_use,
+                               int32_t* largest_batch);
+
+/** Stops the threads: pending requests complete with LUTC_ESHUTDOWN, batches in flight finish; frees everything. */
+LUTC_API int lutc_server_destroy(lutc_server server);
+
 /** Kernel families of the fused path (lutc_tuning.path). */
 #define LUTC_PATH_AUTO 0  /**< TMA-staged kernels when the raster allows them, else strip kernels */
 #define LUTC_PATH_TMA 1   /**< TMA-staged persistent kernels (needs 16-byte aligned rows, width >= 256) */

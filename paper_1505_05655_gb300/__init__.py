@@ -19,7 +19,7 @@ from ._lib import (LUTC_MAX_BANDS, LUTC_STRETCH, Coeffs, LutcError, Raster, chec
 __all__ = ["LutcError", "lib", "version", "lutgen", "apply_u16", "hist", "stretch", "compose", "apply_u8",
            "correct_image_workspace", "correct_image_tables", "correct_image", "apply_stretch", "trace_enable",
            "trace_read", "raster_desc", "coeff_descs", "set_tuning", "reset_tuning", "get_tuning", "Batch",
-           "batch_autotune"]
+           "batch_autotune", "Server"]
 
 
 def _stream(stream, dev):
@@ -324,3 +324,91 @@ def batch_autotune(images, reps: int = 3, stream=None):
     finally:
         b.close()
     return best, ms.value
+
+
+class Server:
+    """The in-process request loop (``lutc_server_*``).
+
+    ``submit`` takes a sensor id, a raster (CUDA uint16 tensor, or a host
+    numpy/pinned tensor with ``host=True``) of ``[bands, H, W]`` and an output
+    of ``[bands, H, W]`` uint8, and returns a ticket; ``wait`` returns the
+    request's :class:`RequestInfo`.  Buffers must stay alive until then.
+    """
+
+    def __init__(self, budget_bytes: int = 0, max_batch: int = 0, max_wait_us: int = 0, streams: int = 0,
+                 max_queue: int = 0, fake_device: bool = False, fake_latency_us: int = 0, fail_every: int = 0):
+        from ._lib import ServerConfig
+        self.cfg = ServerConfig(budget_bytes, max_batch, max_wait_us, streams, max_queue, int(fake_device),
+                                fake_latency_us, fail_every)
+        self._h = ctypes.c_void_p()
+        self._keep = {}
+        check(lib().lutc_server_create(ctypes.byref(self.cfg), ctypes.byref(self._h)), "lutc_server_create")
+
+    def register_sensor(self, sensor_id: int, width: int, bands: int, bits: int, A, G, O) -> None:
+        import numpy as np
+        arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.int32).reshape(bands, width)) for a in (A, G, O)]
+        check(lib().lutc_server_register_sensor(self._h, sensor_id, width, bands, bits, arrs[0].ctypes.data,
+                                                arrs[1].ctypes.data, arrs[2].ctypes.data),
+              "lutc_server_register_sensor")
+
+    @staticmethod
+    def _addr_pitch(t, elem):
+        import numpy as np
+        if isinstance(t, np.ndarray):
+            return t.ctypes.data, t.strides[-2] if t.ndim >= 2 else t.shape[-1] * elem
+        if t.dim() == 3 and t.numel() > 0:
+            return t.data_ptr(), t.stride(1) * elem
+        return t.data_ptr(), t.shape[-1] * elem
+
+    def submit(self, sensor_id: int, raw, out, host: bool = False, keep=None) -> int:
+        """Queues a request; returns its ticket (raises LutcError on refusal, e.g. LUTC_EBUSY)."""
+        from ._lib import LUTC_REQ_HOST
+        ip, pitch = self._addr_pitch(raw, 2)
+        op, opitch = self._addr_pitch(out, 1)
+        h = raw.shape[-2]
+        t = ctypes.c_uint64()
+        rc = lib().lutc_server_submit(self._h, sensor_id, ip, h, pitch, op, opitch, LUTC_REQ_HOST if host else 0,
+                                      ctypes.byref(t))
+        check(rc, "lutc_server_submit")
+        self._keep[t.value] = (raw, out, keep)
+        return t.value
+
+    def try_submit(self, sensor_id: int, raw, out, host: bool = False):
+        """Like submit, but returns (status, ticket) instead of raising."""
+        from ._lib import LUTC_REQ_HOST
+        ip, pitch = self._addr_pitch(raw, 2)
+        op, opitch = self._addr_pitch(out, 1)
+        t = ctypes.c_uint64()
+        rc = lib().lutc_server_submit(self._h, sensor_id, ip, raw.shape[-2], pitch, op, opitch,
+                                      LUTC_REQ_HOST if host else 0, ctypes.byref(t))
+        if rc == 0:
+            self._keep[t.value] = (raw, out, None)
+        return rc, t.value
+
+    def wait(self, ticket: int, timeout_us: int = -1):
+        """The request's RequestInfo, or None if it is still running after timeout_us."""
+        from ._lib import LUTC_ETIMEOUT, RequestInfo
+        info = RequestInfo()
+        rc = lib().lutc_server_wait(self._h, ticket, timeout_us, ctypes.byref(info))
+        if rc == LUTC_ETIMEOUT:
+            return None
+        check(rc, "lutc_server_wait")
+        self._keep.pop(ticket, None)
+        return info
+
+    def stats(self):
+        c, b, u, m = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_size_t(), ctypes.c_int32()
+        check(lib().lutc_server_stats(self._h, ctypes.byref(c), ctypes.byref(b), ctypes.byref(u), ctypes.byref(m)),
+              "lutc_server_stats")
+        return dict(completed=c.value, batches=b.value, budget_in_use=u.value, largest_batch=m.value)
+
+    def close(self) -> None:
+        if self._h:
+            lib().lutc_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -26,6 +26,7 @@ LUTC_TRACE_PHASES = 3
 LUTC_PATH_AUTO = 0
 LUTC_PATH_TMA = 1
 LUTC_PATH_STRIP = 2
+LUTC_REQ_HOST = 2
 
 
 class LutcError(RuntimeError):
@@ -40,6 +41,18 @@ class Coeffs(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("column_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int32), ("max_wait_us", ctypes.c_int32),
+                ("streams", ctypes.c_int32), ("max_queue", ctypes.c_int32), ("fake_device", ctypes.c_int32),
+                ("fake_latency_us", ctypes.c_int32), ("fail_every", ctypes.c_int32)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("batch_size", ctypes.c_int32), ("submit_s", ctypes.c_double),
+                ("start_s", ctypes.c_double), ("done_s", ctypes.c_double), ("cache_miss", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 class Raster(ctypes.Structure):
@@ -82,6 +95,13 @@ SIGNATURES = {
     "lutc_device_status": (_I, [ctypes.POINTER(_I), _P]),
     "lutc_set_tuning": (_I, [_I, ctypes.POINTER(Tuning)]),
     "lutc_batch_workspace": (_SZ, [ctypes.POINTER(Job), _I]),
+    "lutc_server_create": (_I, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]),
+    "lutc_server_register_sensor": (_I, [_P, _I, _I, _I, _I, _P, _P, _P]),
+    "lutc_server_submit": (_I, [_P, _I, _P, _I, _I64, _P, _I64, _I, ctypes.POINTER(ctypes.c_uint64)]),
+    "lutc_server_wait": (_I, [_P, ctypes.c_uint64, _I64, ctypes.POINTER(RequestInfo)]),
+    "lutc_server_stats": (_I, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                               ctypes.POINTER(_SZ), ctypes.POINTER(ctypes.c_int32)]),
+    "lutc_server_destroy": (_I, [_P]),
     "lutc_batch_create": (_I, [ctypes.POINTER(Job), _I, ctypes.POINTER(BatchConfig), _P, _SZ, _P,
                                ctypes.POINTER(_P)]),
     "lutc_batch_run": (_I, [_P, _P]),

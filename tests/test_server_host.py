@@ -1,0 +1,168 @@
+"""Host logic of the request loop, with the fake executor (CPU only, no CUDA call is made).
+
+The fake executor runs no kernel: a batch "completes" fake_latency_us after
+its launch.  Everything else is the real server: the pending queue, the
+batch window (max_batch / max_wait_us), admission against the device-memory
+budget (an allocator over offsets), the streams in flight, tickets, timeouts,
+host-injected batch failures (fail_every) and shutdown.
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import paper_1505_05655_gb300 as lutc
+from paper_1505_05655_gb300 import _lib
+
+W, BANDS, BITS = 300, 2, 12
+
+
+def _server(**kw):
+    s = lutc.Server(fake_device=True, **kw)
+    z = np.zeros((BANDS, W), np.int32)
+    for sid in range(4):
+        s.register_sensor(sid, W, BANDS, BITS, z, z, z)
+    return s
+
+
+def _bufs(h):
+    return np.zeros((BANDS, h, W), np.uint16), np.zeros((BANDS, h, W), np.uint8)
+
+
+def test_requests_complete_and_batch_up():
+    s = _server(max_batch=8, max_wait_us=20000, fake_latency_us=2000)
+    tickets = []
+    keep = []
+    for i in range(40):
+        raw, out = _bufs(16)
+        keep.append((raw, out))
+        tickets.append(s.submit(i % 4, raw, out))
+    infos = [s.wait(t) for t in tickets]
+    assert all(i.status == 0 for i in infos)
+    assert max(i.batch_size for i in infos) == 8
+    st = s.stats()
+    assert st["completed"] == 40 and st["largest_batch"] == 8 and 5 <= st["batches"] <= 40
+    assert st["budget_in_use"] < 64 * 1024  # only the cached coefficients remain
+    s.close()
+
+
+def test_window_holds_a_lone_request_then_launches_it():
+    s = _server(max_batch=32, max_wait_us=60000, fake_latency_us=100)
+    raw, out = _bufs(8)
+    t0 = time.perf_counter()
+    info = s.wait(s.submit(0, raw, out))
+    waited = info.start_s - info.submit_s
+    assert info.status == 0 and info.batch_size == 1
+    assert 0.05 <= waited < 1.0, waited
+    assert time.perf_counter() - t0 >= 0.05
+    # a full batch does not wait for the window
+    ts = [s.submit(1, *_bufs(8)) for _ in range(32)]
+    infos = [s.wait(t) for t in ts]
+    assert max(i.start_s - i.submit_s for i in infos) < 0.05
+    s.close()
+
+
+def test_first_request_of_a_sensor_is_the_cache_miss():
+    s = _server(max_batch=1, max_wait_us=1, fake_latency_us=100)
+    infos = [s.wait(s.submit(2, *_bufs(4))) for _ in range(3)]
+    assert [i.cache_miss for i in infos] == [1, 0, 0]
+    s.close()
+
+
+def test_admission_never_exceeds_the_budget():
+    # host requests need staging: 2 bands x 100 rows x (608 + 304) bytes = 182 KB each;
+    # a 1 MiB budget admits only a few at a time, the rest wait in the queue
+    budget = 1 << 20
+    s = _server(budget_bytes=budget, max_batch=16, max_wait_us=1000, fake_latency_us=20000, streams=4)
+    peak = [0]
+    stop = threading.Event()
+
+    def watch():
+        while not stop.is_set():
+            peak[0] = max(peak[0], s.stats()["budget_in_use"])
+            time.sleep(0.001)
+
+    th = threading.Thread(target=watch)
+    th.start()
+    ts = [s.submit(i % 4, *_bufs(100), host=True) for i in range(24)]
+    infos = [s.wait(t) for t in ts]
+    stop.set()
+    th.join()
+    assert all(i.status == 0 for i in infos)
+    assert 0 < peak[0] <= budget
+    assert max(i.batch_size for i in infos) < 16  # memory, not max_batch, bounded the batches
+    s.close()
+
+
+def test_request_larger_than_the_budget_is_refused():
+    s = _server(budget_bytes=256 << 10, fake_latency_us=10)
+    with pytest.raises(lutc.LutcError) as e:
+        s.submit(0, *_bufs(2000), host=True)
+    assert e.value.status == _lib.LUTC_EBUSY
+    s.close()
+
+
+def test_full_queue_refuses():
+    s = _server(max_queue=4, max_batch=1, max_wait_us=1, streams=1, fake_latency_us=200000)
+    codes = [s.try_submit(0, *_bufs(4))[0] for _ in range(12)]
+    assert _lib.LUTC_EBUSY in codes and codes[0] == 0
+    s.close()
+
+
+def test_wait_times_out_while_running():
+    s = _server(max_batch=1, max_wait_us=1, fake_latency_us=300000)
+    t = s.submit(0, *_bufs(4))
+    assert s.wait(t, timeout_us=1000) is None  # still running: the ticket stays valid
+    info = s.wait(t)
+    assert info.status == 0
+    with pytest.raises(lutc.LutcError):
+        s.wait(t)  # forgotten after completion
+    s.close()
+
+
+def test_injected_batch_failures_are_reported_per_request():
+    s = _server(max_batch=1, max_wait_us=1, fake_latency_us=100, fail_every=3)
+    infos = [s.wait(s.submit(0, *_bufs(4))) for _ in range(9)]
+    failed = [i.status for i in infos]
+    assert failed.count(_lib.LUTC_ECUDA) == 3 and failed.count(0) == 6
+    s.close()
+
+
+def test_unknown_sensor_and_bad_arguments():
+    s = _server()
+    with pytest.raises(lutc.LutcError):
+        s.submit(99, *_bufs(4))
+    with pytest.raises(lutc.LutcError):
+        s.register_sensor(0, W, BANDS, BITS, np.zeros((BANDS, W)), np.zeros((BANDS, W)), np.zeros((BANDS, W)))
+    s.close()
+
+
+def test_shutdown_with_work_pending_does_not_hang():
+    s = _server(max_batch=2, max_wait_us=1, streams=1, fake_latency_us=50000)
+    for _ in range(20):
+        s.submit(0, *_bufs(4))
+    t0 = time.perf_counter()
+    s.close()  # in-flight batch drains, pending requests end with LUTC_ESHUTDOWN
+    assert time.perf_counter() - t0 < 5
+
+
+def test_concurrent_submitters():
+    s = _server(max_batch=16, max_wait_us=500, fake_latency_us=500, streams=3)
+    results = []
+    lock = threading.Lock()
+
+    def client(k):
+        for _ in range(25):
+            info = s.wait(s.submit(k % 4, *_bufs(8)))
+            with lock:
+                results.append(info.status)
+
+    ths = [threading.Thread(target=client, args=(k,)) for k in range(6)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    assert len(results) == 150 and all(r == 0 for r in results)
+    assert s.stats()["completed"] == 150
+    s.close()
