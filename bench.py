@@ -333,6 +333,29 @@ def run_lutc(args, wl):
         line["cpu_baseline"], line["parity"] = cpu_baseline(wl, raw_h.numpy(), A, G, O, out_h.numpy())
     if ws > 1:
         dist.destroy_process_group()
+    if rank == 0 and ws == 1 and wl.name == "scene" and not args.quick:
+        # the metric also names the batched and the served paths: summaries of both
+        import copy
+        sub = copy.copy(args)
+        sub._return = True
+        sub.steps, sub.warmup, sub.no_tune, sub.batch_images = 20, 3, False, 256
+        del raw, out, raw_h, out_h
+        torch.cuda.empty_cache()
+        b = run_batch(sub)
+        line["batched"] = {"value": b["value"], "unit": UNIT, "ms_per_step": b["ms_per_step"],
+                           "images": b["config"]["images"], "pixels_per_step": b["config"]["pixels_per_step"],
+                           "hbm_frac_step": b["hbm_frac_step"], "vs_fused_single": b["value"] / value,
+                           "sequential_calls": b["sequential_calls"]["value"], "autotuned": b["config"]["autotuned"],
+                           "parity": b.get("parity"), "phases_ms": b["phases_ms"]}
+        torch.cuda.empty_cache()
+        sub.steps = 1000
+        v = run_serve(sub)
+        line["served"] = {"saturation_gpx_s": v["saturation"]["gpx_s"],
+                          "vs_fused_single": v["saturation"]["gpx_s"] / value,
+                          "latency_ms": {r: {"p50": d["p50_ms"], "p99": d["p99_ms"], "gpx_s": d["gpx_s"],
+                                             "mean_batch": d["mean_batch"]} for r, d in v["latency"].items()},
+                          "outputs_equal_single_calls": v["outputs_equal_single_calls"],
+                          "config": v["config"]["workload"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -500,6 +523,8 @@ def run_batch(args):
                                           % (",".join(map(str, sample)), px, dt)}
         line["parity"] = {"bit_exact_vs_oracle": same, "pixels_compared": px}
     batch.close()
+    if getattr(args, "_return", False):
+        return line
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -526,9 +551,13 @@ def run_serve(args):
         _, hs, _, _ = synth.batch_spec(synth.SERVE_SEED + 1 + sid, pool_per_sensor)
         for k in range(pool_per_sensor):
             H = int(hs[k])
-            raw = torch.from_numpy(synth.raster(synth.batch_image_seed(synth.SERVE_SEED + 100 + sid, k), B, H, W,
-                                                Bt)).to(device)
-            out = torch.empty((B, H, W), dtype=torch.uint8, device=device)
+            # rows padded to 16 bytes (the TMA path's alignment), bands stacked at H x pitch
+            pitch = -(-W // 8) * 8
+            host = np.zeros((B, H, pitch), np.uint16)
+            synth.raster(synth.batch_image_seed(synth.SERVE_SEED + 100 + sid, k), B, H, W, Bt, out=host[:, :, :W])
+            raw = torch.from_numpy(host).to(device)[:, :, :W]
+            opitch = -(-W // 16) * 16
+            out = torch.empty((B, H, opitch), dtype=torch.uint8, device=device)[:, :, :W]
             pool.append((sid, raw, out, B * H * W))
     rng = np.random.default_rng(synth.SERVE_SEED)
 
@@ -565,9 +594,12 @@ def run_serve(args):
         px = sum(pool[j][3] for j in picks)
         span = max(i.done_s for i in infos) - min(i.submit_s for i in infos)
         bad = sum(1 for i in infos if i.status != 0)
+        prep = np.array([i.launched_s - i.start_s for i in infos])
+        run = np.array([i.done_s - i.launched_s for i in infos])
         return dict(p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
                     gpx_s=px / span / 1e9, mean_batch=float(np.mean([i.batch_size for i in infos])),
-                    requests=n, failed=bad, offered_gpx_s=(px / n) * rate / 1e9 if rate else None)
+                    requests=n, failed=bad, offered_gpx_s=(px / n) * rate / 1e9 if rate else None,
+                    batch_prep_ms=float(np.median(prep) * 1e3), launch_to_done_ms=float(np.median(run) * 1e3))
 
     warm = drive(400, 200)  # first requests of every sensor upload its coefficients
     loads = {}
@@ -592,6 +624,8 @@ def run_serve(args):
                        "l2": "inputs larger than L2 (pool %.1f GB)" % (sum(p_[3] for p_ in pool) * 2 / 1e9)},
             "latency": loads, "saturation": sat, "warmup_with_cache_misses": warm, "server": st,
             "outputs_equal_single_calls": exact}
+    if getattr(args, "_return", False):
+        return line
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -608,6 +642,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--batch-images", type=int, default=256, help="images in the batch workload")
     ap.add_argument("--no-tune", action="store_true", help="batch workload: automatic configuration, no autotuner")
+    ap.add_argument("--quick", action="store_true", help="scene line only (no batch and serving summaries)")
     args = ap.parse_args()
     if args.workload == "batch" and args.impl != "reference":
         run_batch(args)

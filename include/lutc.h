@@ -286,7 +286,8 @@ typedef struct {
     int32_t status;      /**< LUTC_OK, LUTC_ECUDA (failed batch), LUTC_ESHUTDOWN (server closed first) */
     int32_t batch_size;  /**< requests in the batch that carried it */
     double submit_s;     /**< host steady-clock seconds at submit */
-    double start_s;      /**< ... when its batch was launched */
+    double start_s;      /**< ... when its batch was formed */
+    double launched_s;   /**< ... when its batch's work had been enqueued */
     double done_s;       /**< ... when its batch was seen complete */
     int32_t cache_miss;  /**< 1 if this request uploaded its sensor's coefficients */
     int32_t pad;

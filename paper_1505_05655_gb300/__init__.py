@@ -353,10 +353,15 @@ class Server:
 
     @staticmethod
     def _addr_pitch(t, elem):
+        """(address, row pitch in bytes) of a [bands, H, W] buffer whose bands are stacked at H x pitch."""
         import numpy as np
         if isinstance(t, np.ndarray):
+            if t.ndim == 3 and t.shape[0] > 1 and t.strides[0] != t.shape[1] * t.strides[1]:
+                raise ValueError("bands must be stacked at rows x pitch")
             return t.ctypes.data, t.strides[-2] if t.ndim >= 2 else t.shape[-1] * elem
         if t.dim() == 3 and t.numel() > 0:
+            if t.shape[0] > 1 and t.stride(0) != t.shape[1] * t.stride(1):
+                raise ValueError("bands must be stacked at rows x pitch")
             return t.data_ptr(), t.stride(1) * elem
         return t.data_ptr(), t.shape[-1] * elem
 

@@ -51,7 +51,8 @@ class ServerConfig(ctypes.Structure):
 
 class RequestInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("batch_size", ctypes.c_int32), ("submit_s", ctypes.c_double),
-                ("start_s", ctypes.c_double), ("done_s", ctypes.c_double), ("cache_miss", ctypes.c_int32),
+                ("start_s", ctypes.c_double), ("launched_s", ctypes.c_double), ("done_s", ctypes.c_double),
+                ("cache_miss", ctypes.c_int32),
                 ("pad", ctypes.c_int32)]
 
 

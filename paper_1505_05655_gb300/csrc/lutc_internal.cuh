@@ -93,6 +93,8 @@ struct BatchLaunch {
 // TMA path (lutc_tma.cu)
 bool tma_encode(CUtensorMap* map, const lutc_raster* in, int column_threads);
 int tma_box_rows(int column_threads);
+int tma_preload();     // loads every TMA kernel variant, caches occupancies
+int tables_preload();  // loads the scan kernels
 int tma_batch_pass(const BatchLaunch& b, int mode, int column_threads, int blocks_per_sm, cudaStream_t st);
 int launch_stretch(const unsigned long long* hist, int bands, int bits, uint8_t* S, int32_t* lohi, cudaStream_t st);
 int stretch_batch(const TableDesc* tables, int ntables, const unsigned long long* hist, uint8_t* S, int32_t* lohi,

@@ -111,7 +111,7 @@ struct Request {
     int64_t pitch = 0;
     uint8_t* out = nullptr;
     int64_t out_pitch = 0;
-    double t_submit = 0, t_start = 0, t_done = 0;
+    double t_submit = 0, t_start = 0, t_launched = 0, t_done = 0;
     int status = LUTC_OK, batch_size = 0, cache_miss = 0;
     bool done = false;
     size_t in_off = 0, in_bytes = 0, out_off = 0, out_bytes = 0;  // staging (host requests)
@@ -403,7 +403,9 @@ void lutc_server_st::run_batcher()
         if (cfg.fail_every > 0 && number % (uint64_t)cfg.fail_every == 0) rc = LUTC_ECUDA;  // injected on the host
         f->status = rc;
         if (rc && !cfg.fake_device) cudaGetLastError();
+        const double t1 = now_s();
         lk.lock();
+        for (Request* r : f->reqs) r->t_launched = t1;
         // an uploaded sensor stays cached even if its batch failed later; after a failed upload
         // (no kernel of this batch was launched) its memory is returned and the next request retries
         for (Sensor* sp : up) {
@@ -495,7 +497,7 @@ extern "C" int lutc_server_create(const lutc_server_config* config, lutc_server*
     if (!s) return LUTC_ENOMEM;
     s->cfg = c;
     if (!c.fake_device) {
-        if (cudaGetDevice(&s->device) != cudaSuccess ||
+        if (cudaGetDevice(&s->device) != cudaSuccess || tma_preload() != LUTC_OK || tables_preload() != LUTC_OK ||
             cudaMalloc(&s->base, c.budget_bytes) != cudaSuccess) {
             cudaGetLastError();
             delete s;
@@ -596,6 +598,7 @@ extern "C" int lutc_server_wait(lutc_server s, uint64_t ticket, int64_t timeout_
         info->batch_size = r->batch_size;
         info->submit_s = r->t_submit;
         info->start_s = r->t_start;
+        info->launched_s = r->t_launched;
         info->done_s = r->t_done;
         info->cache_miss = r->cache_miss;
         info->pad = 0;

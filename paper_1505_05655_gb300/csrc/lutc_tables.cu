@@ -247,6 +247,14 @@ int launch_stretch(const unsigned long long* hist, int bands, int bits, uint8_t*
     return cuda_status(cudaGetLastError());
 }
 
+int tables_preload()
+{
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_stretch) != cudaSuccess) return LUTC_ECUDA;
+    if (cudaFuncGetAttributes(&fa, k_stretch_batch) != cudaSuccess) return LUTC_ECUDA;
+    return LUTC_OK;
+}
+
 int stretch_batch(const TableDesc* tables, int ntables, const unsigned long long* hist, uint8_t* S, int32_t* lohi,
                   cudaStream_t st)
 {

@@ -35,7 +35,11 @@
 #include <cudaTypedefs.h>
 #include <stdint.h>
 
+#include <map>
 #include <mutex>
+#include <set>
+#include <tuple>
+#include <utility>
 
 #include "lutc_internal.cuh"
 
@@ -208,6 +212,57 @@ __device__ __forceinline__ void store8x16(uint8_t* dst, const uint32_t (&d)[8])
         uint16_t* p = reinterpret_cast<uint16_t*>(dst);
 #pragma unroll
         for (int k = 0; k < 8; ++k) p[k] = (uint16_t)d[k];
+    }
+}
+
+// One row of a thread's 8 pixels through pass MODE.  kFull: all 8 columns exist; otherwise the
+// first n do and the rest (TMA zero fill past the image edge) are masked out.
+template <int MODE, bool kFull>
+__device__ __forceinline__ void row8(const uint4 v, int n, const int32_t (&A)[8], const int32_t (&G)[8],
+                                     const int32_t (&O)[8], int32_t M, uint32_t M2, uint32_t* hs,
+                                     unsigned long long* hb, const unsigned char* table, uint8_t* dst, int vout)
+{
+    uint32_t x[8], d[8];
+    unpack_clamped(v, M2, x);
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) d[jj] = det_horner(A[jj], G[jj], O[jj], x[jj], M);
+    if (MODE == kModeHist) {
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+            if (kFull || jj < n) atomicAdd(hs + d[jj], 1u);
+    } else if (MODE == kModeHistGlobal) {
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+            if (kFull || jj < n) atomicAdd(hb + d[jj], 1ull);
+    } else if (MODE == kModeApplyStretch) {
+        uint32_t o[8];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) o[jj] = table[d[jj]];
+        if (kFull) {
+            const uint32_t lo = o[0] | (o[1] << 8) | (o[2] << 16) | (o[3] << 24);
+            const uint32_t hi = o[4] | (o[5] << 8) | (o[6] << 16) | (o[7] << 24);
+            if (vout) *reinterpret_cast<uint2*>(dst) = make_uint2(lo, hi);
+            else store8(dst, lo, hi);
+        } else {
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj)
+                if (jj < n) dst[jj] = (uint8_t)o[jj];
+        }
+    } else {
+        if (kFull) {
+            if (vout) {
+                uint4 r;
+                r.x = d[0] | (d[1] << 16); r.y = d[2] | (d[3] << 16);
+                r.z = d[4] | (d[5] << 16); r.w = d[6] | (d[7] << 16);
+                *reinterpret_cast<uint4*>(dst) = r;
+            } else {
+                store8x16(dst, d);
+            }
+        } else {
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj)
+                if (jj < n) reinterpret_cast<uint16_t*>(dst)[jj] = (uint16_t)d[jj];
+        }
     }
 }
 
@@ -408,56 +463,23 @@ __global__ void __launch_bounds__(kThreads) k_tma_strip(const __grid_constant__ 
         const int64_t orow0 = (int64_t)band * J.H + row + ph;
         if (fits && n > 0) {
             // int32-exact columns; a right-edge chunk (n < 8) reads TMA's zero fill past the
-            // edge and masks those pixels out, so it runs at full speed too
+            // edge and masks those pixels out, so it stays on this path too
+            const int64_t esize = MODE == kApplyDetector ? 2 : 1;
+            uint8_t* out0 = MODE >= kApplyStretch ? J.out + orow0 * J.out_pitch + (int64_t)c0 * esize : nullptr;
+            if (n == 8) {
 #pragma unroll
-            for (int i = 0; i < kRowsPerThread; ++i) {
-                if (ph + i * P < nrows) {
-                    const uint4 v = *reinterpret_cast<const uint4*>(tile + i * P * 512);
-                    uint32_t x[8], d[8];
-                    unpack_clamped(v, M2, x);
-#pragma unroll
-                    for (int jj = 0; jj < 8; ++jj) d[jj] = det_horner(A[jj], G[jj], O[jj], x[jj], M);
-                    if (MODE == kHist) {
-#pragma unroll
-                        for (int jj = 0; jj < 8; ++jj)
-                            if (jj < n) atomicAdd(hs + d[jj], 1u);
-                    } else if (MODE == kHistGlobal) {
-#pragma unroll
-                        for (int jj = 0; jj < 8; ++jj)
-                            if (jj < n) atomicAdd(hb + d[jj], 1ull);
-                    } else if (MODE == kApplyStretch) {
-                        uint32_t o[8];
-#pragma unroll
-                        for (int jj = 0; jj < 8; ++jj) o[jj] = table[d[jj]];
-                        uint8_t* dst = J.out + (orow0 + i * P) * J.out_pitch + c0;
-                        const uint32_t lo = o[0] | (o[1] << 8) | (o[2] << 16) | (o[3] << 24);
-                        const uint32_t hi = o[4] | (o[5] << 8) | (o[6] << 16) | (o[7] << 24);
-                        if (n == 8) {
-                            if (J.vout) *reinterpret_cast<uint2*>(dst) = make_uint2(lo, hi);
-                            else store8(dst, lo, hi);
-                        } else {
-#pragma unroll
-                            for (int jj = 0; jj < 8; ++jj)
-                                if (jj < n) dst[jj] = (uint8_t)o[jj];
-                        }
-                    } else {
-                        uint8_t* dst = J.out + (orow0 + i * P) * J.out_pitch + (int64_t)c0 * 2;
-                        if (n == 8) {
-                            if (J.vout) {
-                                uint4 r;
-                                r.x = d[0] | (d[1] << 16); r.y = d[2] | (d[3] << 16);
-                                r.z = d[4] | (d[5] << 16); r.w = d[6] | (d[7] << 16);
-                                *reinterpret_cast<uint4*>(dst) = r;
-                            } else {
-                                store8x16(dst, d);
-                            }
-                        } else {
-#pragma unroll
-                            for (int jj = 0; jj < 8; ++jj)
-                                if (jj < n) reinterpret_cast<uint16_t*>(dst)[jj] = (uint16_t)d[jj];
-                        }
-                    }
-                }
+                for (int i = 0; i < kRowsPerThread; ++i)
+                    if (ph + i * P < nrows)
+                        row8<MODE, true>(*reinterpret_cast<const uint4*>(tile + i * P * 512), 8, A, G, O, M, M2,
+                                         hs, hb, table, out0 + (MODE >= kApplyStretch ? i * P * J.out_pitch : 0),
+                                         J.vout);
+            } else {
+#pragma unroll 1
+                for (int i = 0; i < kRowsPerThread; ++i)
+                    if (ph + i * P < nrows)
+                        row8<MODE, false>(*reinterpret_cast<const uint4*>(tile + i * P * 512), n, A, G, O, M, M2,
+                                          hs, hb, table, out0 + (MODE >= kApplyStretch ? i * P * J.out_pitch : 0),
+                                          J.vout);
             }
         } else if (n > 0) {
             // a column that needs int64: exact, slow, few registers
@@ -537,15 +559,39 @@ size_t table_bytes(int mode, int max_bits)
     return mode == kHist ? L * 4 : (mode == kApplyStretch ? L : 0);
 }
 
-// Grid = SMs x resident blocks (capped by blocks_per_sm when > 0), one wave.
+constexpr size_t kMaxSmem = (size_t)kRingBytes + 128 + ((size_t)4 << 15);  // 15-bit histogram
+
+// Grid = SMs x resident blocks (capped by blocks_per_sm when > 0), one wave.  The kernel's
+// shared-memory limit is raised once to the largest any launch uses, and the occupancy of each
+// (kernel, shared size) is computed once per device: a launch then costs no attribute change
+// and no occupancy query.
 template <class K>
 int grid_for(K k, size_t smem, int blocks_per_sm, int64_t* grid)
 {
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return LUTC_ECUDA;
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> raised;                 // (kernel, device)
+    static std::map<std::tuple<const void*, int, size_t>, int> occ;     // (kernel, device, smem) -> blocks/SM
+    const void* key = reinterpret_cast<const void*>(k);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LUTC_ECUDA;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem) != cudaSuccess || per_sm < 1)
-        return LUTC_ECUDA;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!raised.count({key, dev})) {
+            if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) != cudaSuccess)
+                return LUTC_ECUDA;
+            raised.insert({key, dev});
+        }
+        auto it = occ.find(std::make_tuple(key, dev, smem));
+        if (it != occ.end()) {
+            per_sm = it->second;
+        } else {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem) != cudaSuccess ||
+                per_sm < 1)
+                return LUTC_ECUDA;
+            occ[std::make_tuple(key, dev, smem)] = per_sm;
+        }
+    }
     if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
     *grid = (int64_t)sm_count() * per_sm;
     return LUTC_OK;
@@ -600,7 +646,37 @@ int launch_batch(BatchArgs& a, int tc, int blocks_per_sm, cudaStream_t st)
     }
 }
 
+template <int TC>
+int preload_tc()
+{
+    int64_t g = 0;
+    int rc = LUTC_OK;
+    for (int bits = LUTC_MIN_BITS; bits <= 15 && !rc; ++bits) {
+        const size_t h = (size_t)kRingBytes + 128 + table_bytes(kHist, bits);
+        const size_t t = (size_t)kRingBytes + 128 + table_bytes(kApplyStretch, bits);
+        const size_t z = (size_t)kRingBytes + 128;
+        if (!rc) rc = grid_for(k_tma_strip<TC, kHist, false, TmaArgs>, h, 0, &g);
+        if (!rc) rc = grid_for(k_tma_strip<TC, kHist, true, BatchArgs>, h, 0, &g);
+        if (!rc) rc = grid_for(k_tma_strip<TC, kApplyStretch, false, TmaArgs>, t, 0, &g);
+        if (!rc) rc = grid_for(k_tma_strip<TC, kApplyStretch, true, BatchArgs>, t, 0, &g);
+        if (!rc) rc = grid_for(k_tma_strip<TC, kApplyDetector, false, TmaArgs>, z, 0, &g);
+        if (!rc) rc = grid_for(k_tma_strip<TC, kApplyDetector, true, BatchArgs>, z, 0, &g);
+    }
+    if (!rc) rc = grid_for(k_tma_strip<TC, kHistGlobal, false, TmaArgs>, (size_t)kRingBytes + 128, 0, &g);
+    return rc;
+}
+
 }  // namespace
+
+// Loads every TMA kernel variant and caches its occupancy, so that no launch pays a first-use
+// cost (module loading, attribute change) in the middle of a latency-sensitive stream of work.
+int tma_preload()
+{
+    int rc = preload_tc<64>();
+    if (!rc) rc = preload_tc<128>();
+    if (!rc) rc = preload_tc<256>();
+    return rc;
+}
 
 int tma_box_rows(int column_threads) { return kTileBytes / (16 * column_threads); }
 
@@ -611,9 +687,13 @@ bool tma_encode(CUtensorMap* map, const lutc_raster* in, int column_threads)
     const cuuint64_t strides[1] = {(cuuint64_t)in->pitch_bytes};
     const cuuint32_t box[2] = {256, (cuuint32_t)tma_box_rows(column_threads)};
     const cuuint32_t estr[2] = {1, 1};
+    // Wide strips read 4 KB of each row per tile: letting L2 fill 256-byte blocks helps there.
+    // Narrow strips of short, unaligned rows would pull in neighbouring bytes nobody reads.
+    const CUtensorMapL2promotion promo =
+        column_threads >= 256 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_NONE;
     return encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<uint16_t*>(in->data), dims, strides, box,
-                       estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                       CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+                       estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, promo,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 bool tma_eligible(const lutc_raster* in)
