@@ -18,6 +18,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
+#include <cmath>
 #include <new>
 #include <vector>
 
@@ -29,13 +31,60 @@ namespace {
 
 enum Kind { kTmaStretch = 0, kTmaDetector = 1, kFallback = 2 };
 
+// Pass 1 keeps a 2^bits x 4-byte histogram per block in shared memory: up to 12 bits it is small
+// enough for 3 blocks per SM, above that only 2 fit.  Stretch jobs are therefore ordered
+// small-table first and pass 1 runs as two launches, one per class.
+constexpr int kSmallBits = 12;
+
+// Each launch's blocks get contiguous runs of units (strip rows) of about equal cost.  A strip
+// row's cost is modelled as its valid columns plus kRowOverhead: measured on GB300, a row of a
+// narrow right-edge strip costs about as much as a full one (the tile's round trip through the
+// shared-memory ring dominates), so the overhead term is a full strip's width.
+constexpr int kMaxGrid = 2048;
+constexpr int kLaunches = 4;  // pass 1 (small tables), pass 1 (large tables), pass 2, detector only
+constexpr int64_t kRowOverhead = 2048;
+
+void partition(const JobDesc* J, int n, int SW, int grid, int64_t* starts)
+{
+    if (n == 0) {
+        for (int k = 0; k <= grid; ++k) starts[k] = 0;
+        return;
+    }
+    const JobDesc& last = J[n - 1];
+    const int64_t u_end = last.unit_begin + (int64_t)last.bands * last.strips * last.H;
+    double total = 0.0;
+    for (int j = 0; j < n; ++j)
+        for (int s = 0; s < J[j].strips; ++s)
+            total += (double)J[j].bands * J[j].H * (double)(std::min(SW, J[j].W - s * SW) + kRowOverhead);
+    const double per = total / grid;
+    int k = 1;
+    starts[0] = J[0].unit_begin;
+    double acc = 0.0;
+    for (int j = 0; j < n; ++j)
+        for (int band = 0; band < J[j].bands; ++band)
+            for (int s = 0; s < J[j].strips; ++s) {
+                const double c = (double)(std::min(SW, J[j].W - s * SW) + kRowOverhead);
+                const double seg = c * J[j].H;
+                const int64_t u_seg = J[j].unit_begin + ((int64_t)band * J[j].strips + s) * J[j].H;
+                while (k < grid && acc + seg >= per * k) {
+                    int64_t rows = (int64_t)std::ceil((per * k - acc) / c);
+                    rows = rows < 0 ? 0 : (rows > J[j].H ? J[j].H : rows);
+                    starts[k] = std::max(starts[k - 1], u_seg + rows);
+                    ++k;
+                }
+                acc += seg;
+            }
+    while (k <= grid) starts[k++] = u_end;
+}
+
 struct Plan {
     std::vector<int> kind;          // per job
     std::vector<size_t> fb_off;     // per job: workspace offset of a fallback job's own workspace
     std::vector<size_t> fb_bytes;
     std::vector<int64_t> tbl_first; // per job: first TableDesc index (TMA stretch jobs)
     int ns = 0, nd = 0, nbands_s = 0, nbands_d = 0;
-    size_t off_sjobs = 0, off_djobs = 0, off_coef = 0, off_maps = 0, off_tables = 0;
+    int ns_small = 0;  // stretch jobs of <= kSmallBits bits, placed first in the job table
+    size_t off_sjobs = 0, off_djobs = 0, off_coef = 0, off_maps = 0, off_tables = 0, off_part = 0;
     size_t off_hist = 0, off_S = 0, off_lohi = 0, off_fb = 0, total = 0;
     size_t hist_bytes = 0, S_bytes = 0;
     int s_max_bits = 8, d_max_bits = 8;
@@ -76,8 +125,8 @@ int make_plan(const lutc_job* jobs, int n, Plan& p)
         if (batch_tma_ok(jobs[i])) {
             p.kind[i] = stretch ? kTmaStretch : kTmaDetector;
             if (stretch) {
-                p.tbl_first[i] = p.nbands_s;
                 p.ns++;
+                if (jobs[i].in.bits <= kSmallBits) p.ns_small++;
                 p.nbands_s += jobs[i].in.bands;
                 hist_elems += (int64_t)jobs[i].in.bands << jobs[i].in.bits;
                 S_bytes += (int64_t)jobs[i].in.bands << jobs[i].in.bits;
@@ -102,6 +151,8 @@ int make_plan(const lutc_job* jobs, int n, Plan& p)
     o = align_up(o + sizeof(CUtensorMap) * (p.ns + p.nd), 256);
     p.off_tables = o;
     o = align_up(o + sizeof(TableDesc) * p.nbands_s, 256);
+    p.off_part = o;
+    o = align_up(o + sizeof(int64_t) * kLaunches * (kMaxGrid + 1), 256);
     p.off_hist = o;
     p.hist_bytes = (size_t)hist_elems * 8;
     o = align_up(o + p.hist_bytes, 256);
@@ -131,6 +182,9 @@ struct lutc_batch_st {
     uint8_t* ws = nullptr;
     std::vector<uint8_t> blob;  // host image of the descriptor part of the workspace
     int64_t s_units = 0, d_units = 0;
+    int64_t s_units_small = 0;  // units of the first ns_small stretch jobs
+    int small_max_bits = 8;
+    int grid[kLaunches] = {0, 0, 0, 0};
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -164,13 +218,33 @@ int enqueue(lutc_batch b, cudaStream_t st, cudaEvent_t* tr)
         L.hist = reinterpret_cast<unsigned long long*>(b->ws + p.off_hist);
         L.S = b->ws + p.off_S;
         L.S_out = b->ws + p.off_S;
+        L.unit_offset = 0;
         if ((rc = cuda_status(cudaMemsetAsync(L.hist, 0, p.hist_bytes, st)))) return rc;
-        if ((rc = tma_batch_pass(L, kModeHist, tc, bps, st))) return rc;
+        // pass 1 in two launches: small histograms (more blocks per SM), then the rest
+        const int64_t* part = reinterpret_cast<const int64_t*>(b->ws + p.off_part);
+        BatchLaunch L1 = L;
+        L1.njobs = p.ns_small;
+        L1.max_bits = b->small_max_bits;
+        L1.units = b->s_units_small;
+        L1.starts = part;
+        L1.grid = b->grid[0];
+        BatchLaunch L2 = L;
+        L2.jobs = L.jobs + p.ns_small;
+        L2.maps = L.maps + p.ns_small;
+        L2.njobs = p.ns - p.ns_small;
+        L2.unit_offset = b->s_units_small;
+        L2.units = b->s_units - b->s_units_small;
+        L2.starts = part + (kMaxGrid + 1);
+        L2.grid = b->grid[1];
+        if (L1.njobs > 0 && (rc = tma_batch_pass(L1, kModeHist, tc, bps, st))) return rc;
+        if (L2.njobs > 0 && (rc = tma_batch_pass(L2, kModeHist, tc, bps, st))) return rc;
         if (tr) cudaEventRecord(tr[1], st);
         if ((rc = stretch_batch(reinterpret_cast<const TableDesc*>(b->ws + p.off_tables), p.nbands_s, L.hist,
                                 b->ws + p.off_S, reinterpret_cast<int32_t*>(b->ws + p.off_lohi), st)))
             return rc;
         if (tr) cudaEventRecord(tr[2], st);
+        L.starts = part + 2 * (kMaxGrid + 1);
+        L.grid = b->grid[2];
         if ((rc = tma_batch_pass(L, kModeApplyStretch, tc, bps, st))) return rc;
     } else if (tr) {
         cudaEventRecord(tr[1], st);
@@ -182,7 +256,10 @@ int enqueue(lutc_batch b, cudaStream_t st, cudaEvent_t* tr)
         L.maps = reinterpret_cast<const CUtensorMap*>(b->ws + p.off_maps) + p.ns;
         L.njobs = p.nd;
         L.max_bits = p.d_max_bits;
+        L.unit_offset = 0;
         L.units = b->d_units;
+        L.starts = reinterpret_cast<const int64_t*>(b->ws + p.off_part) + 3 * (kMaxGrid + 1);
+        L.grid = b->grid[3];
         L.hist = nullptr;
         L.S = nullptr;
         L.S_out = nullptr;
@@ -257,8 +334,17 @@ extern "C" int lutc_batch_create(const lutc_job* jobs, int n, const lutc_batch_c
     const BandCoef* d_cf = reinterpret_cast<const BandCoef*>(b->ws + p.off_coef);
     int is = 0, id = 0, icf = 0, it = 0;
     int64_t hist_off = 0, S_off = 0;
-    for (int i = 0; i < n; ++i) {
-        if (p.kind[i] == kFallback) continue;
+    // job table order: stretch jobs of <= kSmallBits bits, the other stretch jobs, then detector jobs
+    std::vector<int> order;
+    for (int pass = 0; pass < 3; ++pass)
+        for (int i = 0; i < n; ++i) {
+            if (p.kind[i] == kFallback) continue;
+            const bool stretch = p.kind[i] == kTmaStretch;
+            const bool small = b->jobs[i].in.bits <= kSmallBits;
+            if ((pass == 0 && stretch && small) || (pass == 1 && stretch && !small) || (pass == 2 && !stretch))
+                order.push_back(i);
+        }
+    for (int i : order) {
         const lutc_job& j = b->jobs[i];
         const bool stretch = p.kind[i] == kTmaStretch;
         JobDesc& J = stretch ? sj[is] : dj[id];
@@ -286,6 +372,11 @@ extern "C" int lutc_batch_create(const lutc_job* jobs, int n, const lutc_batch_c
         }
         if (stretch) {
             const int64_t L = (int64_t)1 << j.in.bits;
+            b->plan.tbl_first[i] = it;
+            if (is < p.ns_small) {
+                b->s_units_small = b->s_units;
+                if (j.in.bits > b->small_max_bits) b->small_max_bits = j.in.bits;
+            }
             for (int k = 0; k < j.in.bands; ++k) {
                 tbl[it].hist_off = hist_off + k * L;
                 tbl[it].S_off = S_off + k * L;
@@ -299,6 +390,29 @@ extern "C" int lutc_batch_create(const lutc_job* jobs, int n, const lutc_batch_c
             ++is;
         } else {
             ++id;
+        }
+    }
+    // grids and cost-balanced block boundaries of the four launches
+    {
+        const int bps = b->cfg.blocks_per_sm;
+        struct { const JobDesc* J; int n; int mode; int bits; } L[kLaunches] = {
+            {sj, p.ns_small, kModeHist, b->small_max_bits},
+            {sj + p.ns_small, p.ns - p.ns_small, kModeHist, p.s_max_bits},
+            {sj, p.ns, kModeApplyStretch, p.s_max_bits},
+            {dj, p.nd, kModeApplyDetector, p.d_max_bits}};
+        int64_t* part = reinterpret_cast<int64_t*>(b->blob.data() + p.off_part);
+        for (int l = 0; l < kLaunches; ++l) {
+            int g = 0;
+            if (L[l].n > 0) {
+                g = tma_batch_grid(L[l].mode, tc, L[l].bits, bps);
+                if (g <= 0) {
+                    delete b;
+                    return LUTC_ECUDA;
+                }
+                g = std::min(g, kMaxGrid);
+            }
+            b->grid[l] = g;
+            partition(L[l].J, L[l].n, SW, std::max(g, 1), part + (size_t)l * (kMaxGrid + 1));
         }
     }
     if (p.off_hist > 0) {

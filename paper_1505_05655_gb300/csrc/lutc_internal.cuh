@@ -84,7 +84,10 @@ struct BatchLaunch {
     const CUtensorMap* maps;  // one per job, 64-byte aligned
     int32_t njobs;
     int32_t max_bits;
+    int64_t unit_offset;      // first unit of the launch (jobs[0].unit_begin)
     int64_t units;
+    const int64_t* starts;    // device [grid + 1]: block k walks units [starts[k], starts[k + 1])
+    int32_t grid;
     unsigned long long* hist;
     const uint8_t* S;
     uint8_t* S_out;
@@ -96,6 +99,8 @@ int tma_box_rows(int column_threads);
 int tma_preload();     // loads every TMA kernel variant, caches occupancies
 int tables_preload();  // loads the scan kernels
 int tma_batch_pass(const BatchLaunch& b, int mode, int column_threads, int blocks_per_sm, cudaStream_t st);
+// Blocks of a batch launch (SMs x resident blocks, capped by blocks_per_sm when > 0); 0 on error.
+int tma_batch_grid(int mode, int column_threads, int max_bits, int blocks_per_sm);
 int launch_stretch(const unsigned long long* hist, int bands, int bits, uint8_t* S, int32_t* lohi, cudaStream_t st);
 int stretch_batch(const TableDesc* tables, int ntables, const unsigned long long* hist, uint8_t* S, int32_t* lohi,
                   cudaStream_t st);

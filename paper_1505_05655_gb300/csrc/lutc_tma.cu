@@ -50,10 +50,22 @@ namespace {
 constexpr int kConsumers = 256;            // consumer threads per block (8 warps)
 constexpr int kThreads = kConsumers + 32;  // + one producer warp
 constexpr int kConsumerWarps = kConsumers / 32;
-constexpr int kStages = 3;
-constexpr int kRowsPerThread = 4;          // rows of a tile each consumer thread processes
-constexpr int kTileBytes = kConsumers * 16 * kRowsPerThread;  // 16 KB
+// Ring geometry (compile-time; the product builds the defaults).
+#ifndef LUTC_RING_STAGES
+#define LUTC_RING_STAGES 3
+#endif
+#ifndef LUTC_ROWS_PER_THREAD
+#define LUTC_ROWS_PER_THREAD 4
+#endif
+constexpr int kStages = LUTC_RING_STAGES;
+constexpr int kRowsPerThread = LUTC_ROWS_PER_THREAD;  // rows of a tile each consumer thread processes
+constexpr int kTileBytes = kConsumers * 16 * kRowsPerThread;  // 16 KB with the defaults
 constexpr int kRingBytes = kStages * kTileBytes;
+// mbarriers after the ring (full and empty per stage, one consumer barrier), then the table
+constexpr int kBarRegion = ((2 * kStages + 1) * 8 + 127) / 128 * 128;
+constexpr int kTableOffset = kRingBytes + kBarRegion;
+static_assert((2 * kStages + 1) * 8 <= kBarRegion, "barrier region");
+static_assert(kTableOffset % 128 == 0, "table alignment");
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
 
 enum Mode { kHist = kModeHist, kHistGlobal = kModeHistGlobal, kApplyStretch = kModeApplyStretch,
@@ -79,8 +91,10 @@ struct BatchArgs {
     const CUtensorMap* maps;
     int32_t njobs;
     int32_t max_bits;
+    int64_t unit_offset;  // first unit of this launch (its jobs' unit_begin are absolute)
     int64_t units;
     int64_t units_per_block;
+    const int64_t* starts;  // [gridDim.x + 1] block boundaries in units, balanced by cost
     unsigned long long* hist;
     const uint8_t* S;
 };
@@ -143,6 +157,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
         }
     }
     return true;
+}
+
+// Brings a tensor map held in global memory into the TMA unit's descriptor cache.
+__device__ __forceinline__ void tma_prefetch_map(const CUtensorMap* map)
+{
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y)
@@ -291,7 +311,7 @@ __device__ __forceinline__ BandCoef coef_of(const Args& a, const JobDesc& J, int
 // The launch's work is the concatenation over its jobs of (band, strip, row)
 // units; block k takes units [k q, (k + 1) q) and walks them tile by tile.
 template <int TC, int MODE, bool kBatch, class Args>
-__global__ void __launch_bounds__(kThreads) k_tma_strip(const __grid_constant__ Args a)
+__global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant__ Args a)
 {
     constexpr int SW = 8 * TC;                 // strip width (columns)
     constexpr int P = kConsumers / TC;         // row phases
@@ -304,7 +324,7 @@ __global__ void __launch_bounds__(kThreads) k_tma_strip(const __grid_constant__ 
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + kRingBytes);
     uint64_t* empty = full + kStages;
     uint64_t* csync = empty + kStages;  // consumer-only barrier (band changes)
-    unsigned char* table = smem + kRingBytes + 128;
+    unsigned char* table = smem + kTableOffset;
     uint32_t* hs = reinterpret_cast<uint32_t*>(table);
 
     const int tid = threadIdx.x;
@@ -322,8 +342,14 @@ __global__ void __launch_bounds__(kThreads) k_tma_strip(const __grid_constant__ 
     __syncthreads();
 
     // This block's share of the units, walked without divisions after the first.
-    const int64_t u0 = (int64_t)blockIdx.x * a.units_per_block;
-    const int64_t u1 = min(a.units, u0 + a.units_per_block);
+    int64_t u0, u1;
+    if constexpr (kBatch) {
+        u0 = a.starts[blockIdx.x];
+        u1 = a.starts[blockIdx.x + 1];
+    } else {
+        u0 = (int64_t)blockIdx.x * a.units_per_block;
+        u1 = min(a.units, u0 + a.units_per_block);
+    }
     if (u0 >= u1) return;
     int64_t left = u1 - u0;
     int j = 0;
@@ -353,6 +379,7 @@ __global__ void __launch_bounds__(kThreads) k_tma_strip(const __grid_constant__ 
         if (tid != kConsumers) return;
         int issued = 0;
         bool ok = true;
+        if constexpr (kBatch) tma_prefetch_map(map_of<kBatch>(a, j));
         while (left > 0) {
             const int nrows = (int)min((int64_t)min(RT, J.H - row), left);
             if (issued >= kStages && !mbar_wait(&empty[stage], phase ^ 1u)) {
@@ -375,7 +402,10 @@ __global__ void __launch_bounds__(kThreads) k_tma_strip(const __grid_constant__ 
                     strip = 0;
                     if (++band == J.bands) {
                         band = 0;
-                        if (kBatch && left > 0) J = job_of<kBatch>(a, ++j);
+                        if (kBatch && left > 0) {
+                            J = job_of<kBatch>(a, ++j);
+                            tma_prefetch_map(map_of<kBatch>(a, j));
+                        }
                     }
                 }
             }
@@ -406,6 +436,7 @@ __global__ void __launch_bounds__(kThreads) k_tma_strip(const __grid_constant__ 
     int hb_len = 0;
     int32_t A[8], G[8], O[8];
     bool fits = true;
+    bool masked = false;  // this warp holds the right-edge partial chunk of its strip
     int n = 0, c0 = 0;
     while (left > 0) {
         const int nrows = (int)min((int64_t)min(RT, J.H - row), left);
@@ -457,6 +488,10 @@ __global__ void __launch_bounds__(kThreads) k_tma_strip(const __grid_constant__ 
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) O[jj] += 32768;
             }
+            // A warp with the partial chunk runs the masked path in every lane: running the full
+            // path in 31 lanes and then the masked one in one lane would double the warp's time
+            // per tile, and the ring only advances at its slowest warp's pace.
+            masked = __any_sync(0xffffffffu, n > 0 && n < 8);
         }
         if (!mbar_wait(&full[stage], phase)) return;
         const unsigned char* tile = my + stage * kTileBytes;
@@ -466,7 +501,7 @@ __global__ void __launch_bounds__(kThreads) k_tma_strip(const __grid_constant__ 
             // edge and masks those pixels out, so it stays on this path too
             const int64_t esize = MODE == kApplyDetector ? 2 : 1;
             uint8_t* out0 = MODE >= kApplyStretch ? J.out + orow0 * J.out_pitch + (int64_t)c0 * esize : nullptr;
-            if (n == 8) {
+            if (!masked) {
 #pragma unroll
                 for (int i = 0; i < kRowsPerThread; ++i)
                     if (ph + i * P < nrows)
@@ -474,7 +509,7 @@ __global__ void __launch_bounds__(kThreads) k_tma_strip(const __grid_constant__ 
                                          hs, hb, table, out0 + (MODE >= kApplyStretch ? i * P * J.out_pitch : 0),
                                          J.vout);
             } else {
-#pragma unroll 1
+#pragma unroll
                 for (int i = 0; i < kRowsPerThread; ++i)
                     if (ph + i * P < nrows)
                         row8<MODE, false>(*reinterpret_cast<const uint4*>(tile + i * P * 512), n, A, G, O, M, M2,
@@ -559,7 +594,8 @@ size_t table_bytes(int mode, int max_bits)
     return mode == kHist ? L * 4 : (mode == kApplyStretch ? L : 0);
 }
 
-constexpr size_t kMaxSmem = (size_t)kRingBytes + 128 + ((size_t)4 << 15);  // 15-bit histogram
+constexpr size_t kMaxSmem = (size_t)kTableOffset + ((size_t)4 << 15);  // 15-bit histogram
+static_assert(kMaxSmem <= 232448, "shared memory per block");
 
 // Grid = SMs x resident blocks (capped by blocks_per_sm when > 0), one wave.  The kernel's
 // shared-memory limit is raised once to the largest any launch uses, and the occupancy of each
@@ -601,7 +637,7 @@ template <int TC, int MODE>
 int launch_single_tc(TmaArgs& a, cudaStream_t st)
 {
     auto k = k_tma_strip<TC, MODE, false, TmaArgs>;
-    const size_t smem = (size_t)kRingBytes + 128 + table_bytes(MODE, a.max_bits);
+    const size_t smem = (size_t)kTableOffset + table_bytes(MODE, a.max_bits);
     int64_t grid = 0;
     int rc = grid_for(k, smem, tuning_for(a.job.bits).blocks_per_sm, &grid);
     if (rc) return rc;
@@ -624,25 +660,43 @@ int launch_single(TmaArgs& a, int tc, cudaStream_t st)
 }
 
 template <int TC, int MODE>
-int launch_batch_tc(BatchArgs& a, int blocks_per_sm, cudaStream_t st)
+int launch_batch_tc(BatchArgs& a, int grid, cudaStream_t st)
 {
     auto k = k_tma_strip<TC, MODE, true, BatchArgs>;
-    const size_t smem = (size_t)kRingBytes + 128 + table_bytes(MODE, a.max_bits);
-    int64_t grid = 0;
-    int rc = grid_for(k, smem, blocks_per_sm, &grid);
+    const size_t smem = (size_t)kTableOffset + table_bytes(MODE, a.max_bits);
+    int64_t g = 0;
+    int rc = grid_for(k, smem, 0, &g);  // raises the shared-memory limit on first use
     if (rc) return rc;
-    a.units_per_block = (a.units + grid - 1) / grid;
     k<<<(unsigned)grid, kThreads, smem, st>>>(a);
     return cuda_status(cudaGetLastError());
 }
 
+template <int TC, int MODE>
+int batch_grid_tc(int max_bits, int blocks_per_sm)
+{
+    auto k = k_tma_strip<TC, MODE, true, BatchArgs>;
+    const size_t smem = (size_t)kTableOffset + table_bytes(MODE, max_bits);
+    int64_t g = 0;
+    return grid_for(k, smem, blocks_per_sm, &g) == LUTC_OK ? (int)g : 0;
+}
+
 template <int MODE>
-int launch_batch(BatchArgs& a, int tc, int blocks_per_sm, cudaStream_t st)
+int launch_batch(BatchArgs& a, int tc, int grid, cudaStream_t st)
 {
     switch (tc) {
-    case 256: return launch_batch_tc<256, MODE>(a, blocks_per_sm, st);
-    case 128: return launch_batch_tc<128, MODE>(a, blocks_per_sm, st);
-    default: return launch_batch_tc<64, MODE>(a, blocks_per_sm, st);
+    case 256: return launch_batch_tc<256, MODE>(a, grid, st);
+    case 128: return launch_batch_tc<128, MODE>(a, grid, st);
+    default: return launch_batch_tc<64, MODE>(a, grid, st);
+    }
+}
+
+template <int MODE>
+int batch_grid(int tc, int max_bits, int blocks_per_sm)
+{
+    switch (tc) {
+    case 256: return batch_grid_tc<256, MODE>(max_bits, blocks_per_sm);
+    case 128: return batch_grid_tc<128, MODE>(max_bits, blocks_per_sm);
+    default: return batch_grid_tc<64, MODE>(max_bits, blocks_per_sm);
     }
 }
 
@@ -652,9 +706,9 @@ int preload_tc()
     int64_t g = 0;
     int rc = LUTC_OK;
     for (int bits = LUTC_MIN_BITS; bits <= 15 && !rc; ++bits) {
-        const size_t h = (size_t)kRingBytes + 128 + table_bytes(kHist, bits);
-        const size_t t = (size_t)kRingBytes + 128 + table_bytes(kApplyStretch, bits);
-        const size_t z = (size_t)kRingBytes + 128;
+        const size_t h = (size_t)kTableOffset + table_bytes(kHist, bits);
+        const size_t t = (size_t)kTableOffset + table_bytes(kApplyStretch, bits);
+        const size_t z = (size_t)kTableOffset;
         if (!rc) rc = grid_for(k_tma_strip<TC, kHist, false, TmaArgs>, h, 0, &g);
         if (!rc) rc = grid_for(k_tma_strip<TC, kHist, true, BatchArgs>, h, 0, &g);
         if (!rc) rc = grid_for(k_tma_strip<TC, kApplyStretch, false, TmaArgs>, t, 0, &g);
@@ -662,7 +716,7 @@ int preload_tc()
         if (!rc) rc = grid_for(k_tma_strip<TC, kApplyDetector, false, TmaArgs>, z, 0, &g);
         if (!rc) rc = grid_for(k_tma_strip<TC, kApplyDetector, true, BatchArgs>, z, 0, &g);
     }
-    if (!rc) rc = grid_for(k_tma_strip<TC, kHistGlobal, false, TmaArgs>, (size_t)kRingBytes + 128, 0, &g);
+    if (!rc) rc = grid_for(k_tma_strip<TC, kHistGlobal, false, TmaArgs>, (size_t)kTableOffset, 0, &g);
     return rc;
 }
 
@@ -753,22 +807,35 @@ int tma_apply(const lutc_raster* in, const lutc_coeffs* per_band, const uint8_t*
     return stretch ? launch_single<kApplyStretch>(a, tc, st) : launch_single<kApplyDetector>(a, tc, st);
 }
 
+int tma_batch_grid(int mode, int column_threads, int max_bits, int blocks_per_sm)
+{
+    switch (mode) {
+    case kHist: return batch_grid<kHist>(column_threads, max_bits, blocks_per_sm);
+    case kApplyStretch: return batch_grid<kApplyStretch>(column_threads, max_bits, blocks_per_sm);
+    case kApplyDetector: return batch_grid<kApplyDetector>(column_threads, max_bits, blocks_per_sm);
+    default: return 0;
+    }
+}
+
 int tma_batch_pass(const BatchLaunch& b, int mode, int column_threads, int blocks_per_sm, cudaStream_t st)
 {
-    if (b.units == 0) return LUTC_OK;
+    (void)blocks_per_sm;  // folded into b.grid and b.starts when the batch was planned
+    if (b.units == 0 || b.grid <= 0) return LUTC_OK;
     BatchArgs a;
     a.jobs = b.jobs;
     a.maps = b.maps;
     a.njobs = b.njobs;
     a.max_bits = b.max_bits;
+    a.unit_offset = b.unit_offset;
     a.units = b.units;
     a.units_per_block = 0;
+    a.starts = b.starts;
     a.hist = b.hist;
     a.S = b.S;
     switch (mode) {
-    case kHist: return launch_batch<kHist>(a, column_threads, blocks_per_sm, st);
-    case kApplyStretch: return launch_batch<kApplyStretch>(a, column_threads, blocks_per_sm, st);
-    case kApplyDetector: return launch_batch<kApplyDetector>(a, column_threads, blocks_per_sm, st);
+    case kHist: return launch_batch<kHist>(a, column_threads, b.grid, st);
+    case kApplyStretch: return launch_batch<kApplyStretch>(a, column_threads, b.grid, st);
+    case kApplyDetector: return launch_batch<kApplyDetector>(a, column_threads, b.grid, st);
     default: return LUTC_EUNSUPPORTED;
     }
 }
