@@ -49,23 +49,36 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def csrc_hash() -> str:
+# sources whose change invalidates a committed DRAM-traffic figure, per workload
+TRAFFIC_SOURCES = {
+    "scene": ["csrc/lutc_tma.cu", "csrc/lutc_internal.cuh", "csrc/lutc_correct.cu", "_build.py"],
+    "batch": ["csrc/lutc_tma.cu", "csrc/lutc_internal.cuh", "csrc/lutc_batch.cu", "_build.py"],
+}
+
+
+def csrc_hash(workload: str) -> str:
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1505_05655_gb300", "csrc", "*"))):
-        with open(p, "rb") as f:
-            h.update(os.path.basename(p).encode())
+    for rel in TRAFFIC_SOURCES[workload]:
+        with open(os.path.join(ROOT, "paper_1505_05655_gb300", rel), "rb") as f:
+            h.update(rel.encode())
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on this source."""
+def ncu_traffic(kernel: str, workload: str, units: float | None = None):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on this source.
+
+    Entries with "bytes_per_px" were captured on a smaller case of the same kernel and are
+    scaled to `units` pixels per launch (traffic grows in proportion to the pixels).
+    """
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
         e = t[workload][kernel]
-        if e.get("csrc") != csrc_hash():
+        if e.get("csrc") != csrc_hash(workload):
             return None
+        if "bytes_per_px" in e:
+            return float(e["bytes_per_px"]) * units
         return float(e["bytes_per_launch"])
     except Exception:
         return None
@@ -519,7 +532,8 @@ def run_batch(args):
                                      "graph": True, "tuning_ms": tune_ms}},
             "hbm_frac_step": 5 * pixels / (ms * 1e-3) / 1e9 / peak,
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                         "traffic": None, "kernel": ["pass1 k_tma_strip<hist, batch>", "", "pass2 k_tma_strip<apply, batch>"][dom],
+                         "traffic": ncu_traffic(["pass1", "", "pass2"][dom], "batch", pixels),
+                         "kernel": ["pass1 k_tma_strip<hist, batch>", "", "pass2 k_tma_strip<apply, batch>"][dom],
                          "peak_source": peak_src + " (copy bandwidth)", "alg_bytes_per_launch": alg[dom]},
             "phases_ms": {"pass1_hist": avg[0], "scan": avg[1], "pass2_apply": avg[2]},
             "sequential_calls": {"value": pixels / (seq_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": seq_ms,

@@ -186,6 +186,55 @@ LUTC_API int lutc_apply_stretch(const lutc_raster* in, const lutc_coeffs* per_ba
 LUTC_API int lutc_device_status(int* status, lutc_stream stream);
 
 /* ------------------------------------------------------------------------
+ * The paper's task interface.  A client names a task with a flag, passes a
+ * comma-separated parameter list of at most 200 bytes (sizes of the data
+ * and its element type, among others) and the data, and names where the
+ * result goes (Section II, Fig. 3).  lutc_submit is that call in process;
+ * the data and result buffers are passed as pointer arrays.
+ * ------------------------------------------------------------------------ */
+
+/** Task flags of lutc_submit. */
+enum {
+    LUTC_TASK_LUTGEN = 1,        /**< in {A, G, O}; out {lut}; params width, bits */
+    LUTC_TASK_HIST = 2,          /**< in {raster, A, G, O}; out {hist}; params width, height, bands, bits[, pitch] */
+    LUTC_TASK_STRETCH = 3,       /**< in {hist}; out {S, lohi}; params bands, bits */
+    LUTC_TASK_COMPOSE = 4,       /**< in {lut, S}; out {clut}; params width, bits */
+    LUTC_TASK_APPLY = 5,         /**< in {raster, table}; out {out}; params width, height, bands, bits, table=u16|u8[, pitch, out_pitch] */
+    LUTC_TASK_CORRECT_IMAGE = 6, /**< in {raster, A, G, O}; out {out}; params width, height, bands, bits[, stretch, pitch, out_pitch]; workspace */
+    LUTC_TASK_DEVICE_INFO = 7    /**< out {char buffer} (HOST); params capacity */
+};
+
+#define LUTC_PARAMS_MAX 200 /**< longest parameter string (the paper's 200-byte header field) */
+
+/**
+ * Runs task `task` with parameters `params` ("key=value,key=value", ASCII,
+ * at most LUTC_PARAMS_MAX bytes, no spaces).  A, G, O are device int32 arrays
+ * of [bands][width]; raster and outputs are device buffers with the layouts
+ * of the matching lutc_* call (pitch and out_pitch in bytes default to
+ * packed rows).  workspace is needed by LUTC_TASK_CORRECT_IMAGE with
+ * stretch=1 (lutc_correct_image_workspace bytes); stretch defaults to 1.
+ * Returns the task's status, or LUTC_EINVAL for an unknown task, a malformed,
+ * unknown, missing or out-of-range parameter, or too few buffers; nothing is
+ * enqueued then.
+ */
+LUTC_API int lutc_submit(int task, const char* params, const void* const* inputs, int n_inputs,
+                         void* const* outputs, int n_outputs, void* workspace, size_t workspace_bytes,
+                         lutc_stream stream);
+
+/**
+ * The paper's remote-GPU information utility (Section IV): writes an XML
+ * document listing every visible GPU -- name, compute capability, warp size,
+ * total constant memory, total global memory, shared memory per block, clock
+ * rate, multiprocessor count, registers per block, maximum threads per block,
+ * maximum grid size and maximum block dimensions -- into the HOST buffer xml
+ * of `capacity` bytes (NUL-terminated).  *needed (may be NULL) receives the
+ * bytes the document needs.  Returns LUTC_OK, LUTC_ENOMEM when capacity is
+ * too small (nothing useful written), or LUTC_EINVAL.  With no GPU visible the
+ * document lists none.
+ */
+LUTC_API int lutc_device_info(char* xml, size_t capacity, size_t* needed);
+
+/* ------------------------------------------------------------------------
  * Batches: many independent rasters corrected by one persistent launch per
  * phase.  The paper's server receives tasks from many clients (Sections I-II);
  * a batch is a set of such tasks of uneven size, bit depth and band count,

@@ -19,7 +19,8 @@ from ._lib import (LUTC_MAX_BANDS, LUTC_STRETCH, Coeffs, LutcError, Raster, chec
 __all__ = ["LutcError", "lib", "version", "lutgen", "apply_u16", "hist", "stretch", "compose", "apply_u8",
            "correct_image_workspace", "correct_image_tables", "correct_image", "apply_stretch", "trace_enable",
            "trace_read", "raster_desc", "coeff_descs", "set_tuning", "reset_tuning", "get_tuning", "Batch",
-           "batch_autotune", "Server"]
+           "batch_autotune", "Server", "submit",
+           "device_info"]
 
 
 def _stream(stream, dev):
@@ -417,3 +418,23 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def submit(task: int, params: str, inputs, outputs, workspace: torch.Tensor | None = None, stream=None) -> None:
+    """The paper's task call: a task flag, a "key=value,..." parameter string, data and outputs."""
+    ins = (ctypes.c_void_p * max(1, len(inputs)))(*[t.data_ptr() for t in inputs])
+    outs = (ctypes.c_void_p * max(1, len(outputs)))(*[t.data_ptr() for t in outputs])
+    dev = (inputs or outputs)[0].device
+    ws = workspace.data_ptr() if workspace is not None else None
+    nws = workspace.numel() if workspace is not None else 0
+    check(lib().lutc_submit(task, params.encode(), ins, len(inputs), outs, len(outputs), ws, nws,
+                            _stream(stream, dev)), "lutc_submit")
+
+
+def device_info() -> str:
+    """XML listing of the visible GPUs (the paper's GPU-information utility)."""
+    need = ctypes.c_size_t()
+    lib().lutc_device_info(None, 0, ctypes.byref(need))
+    buf = ctypes.create_string_buffer(need.value)
+    check(lib().lutc_device_info(buf, need.value, ctypes.byref(need)), "lutc_device_info")
+    return buf.value.decode()

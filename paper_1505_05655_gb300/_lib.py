@@ -27,6 +27,8 @@ LUTC_PATH_AUTO = 0
 LUTC_PATH_TMA = 1
 LUTC_PATH_STRIP = 2
 LUTC_REQ_HOST = 2
+LUTC_TASK_LUTGEN, LUTC_TASK_HIST, LUTC_TASK_STRETCH, LUTC_TASK_COMPOSE = 1, 2, 3, 4
+LUTC_TASK_APPLY, LUTC_TASK_CORRECT_IMAGE, LUTC_TASK_DEVICE_INFO = 5, 6, 7
 
 
 class LutcError(RuntimeError):
@@ -95,6 +97,8 @@ SIGNATURES = {
     "lutc_trace_enable": (_I, [_I]),
     "lutc_device_status": (_I, [ctypes.POINTER(_I), _P]),
     "lutc_set_tuning": (_I, [_I, ctypes.POINTER(Tuning)]),
+    "lutc_submit": (_I, [_I, ctypes.c_char_p, ctypes.POINTER(_P), _I, ctypes.POINTER(_P), _I, _P, _SZ, _P]),
+    "lutc_device_info": (_I, [ctypes.c_char_p, _SZ, ctypes.POINTER(_SZ)]),
     "lutc_batch_workspace": (_SZ, [ctypes.POINTER(Job), _I]),
     "lutc_server_create": (_I, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]),
     "lutc_server_register_sensor": (_I, [_P, _I, _I, _I, _I, _P, _P, _P]),

@@ -109,3 +109,36 @@ def test_empty_inputs_need_no_device_work():
     r = _raster(width=0, data=0)
     assert lib.lutc_apply_u8(ctypes.byref(r), ctypes.c_void_p(0x40000), ctypes.c_void_p(0x60000), 0, None) == 0
     assert lib.lutc_correct_image(ctypes.byref(r), zero, 0, None, 0, None, 0, None) == 0
+
+
+@pytest.mark.parametrize("params", ["width=10,bits=12,colour=3", "width=10,bits=", "width=-1,bits=12", "width=10;bits=12",
+                                    "width=10,bits=12," + "x" * 200, "width=10,bits=99", "table=u32,width=1,bits=12",
+                                    "width=10"])
+def test_submit_rejects_bad_parameter_strings(params):
+    lib = _lib.lib()
+    bufs = (ctypes.c_void_p * 4)(0x1000, 0x2000, 0x3000, 0x4000)
+    assert lib.lutc_submit(_lib.LUTC_TASK_LUTGEN, params.encode(), bufs, 3, bufs, 1, None, 0, None) == _lib.LUTC_EINVAL
+
+
+def test_submit_rejects_unknown_task_and_missing_buffers():
+    lib = _lib.lib()
+    bufs = (ctypes.c_void_p * 4)(0x1000, 0x2000, 0x3000, 0x4000)
+    assert lib.lutc_submit(42, b"width=10,bits=12", bufs, 3, bufs, 1, None, 0, None) == _lib.LUTC_EINVAL
+    assert lib.lutc_submit(_lib.LUTC_TASK_LUTGEN, b"width=10,bits=12", bufs, 2, bufs, 1, None, 0, None) == _lib.LUTC_EINVAL
+    assert lib.lutc_submit(_lib.LUTC_TASK_CORRECT_IMAGE, b"width=10,height=4,bits=12", bufs, 4, bufs, 0, None, 0,
+                           None) == _lib.LUTC_EINVAL
+    # a zero-sized task is valid and needs no device
+    assert lib.lutc_submit(_lib.LUTC_TASK_LUTGEN, b"width=0,bits=12", bufs, 3, bufs, 1, None, 0, None) == 0
+
+
+def test_device_info_document_is_well_formed():
+    import xml.etree.ElementTree as ET
+    lib = _lib.lib()
+    need = ctypes.c_size_t()
+    assert lib.lutc_device_info(None, 0, ctypes.byref(need)) == _lib.LUTC_ENOMEM and need.value > 10
+    buf = ctypes.create_string_buffer(need.value)
+    assert lib.lutc_device_info(buf, need.value, None) == 0
+    root = ET.fromstring(buf.value.decode())
+    assert root.tag == "gpus" and int(root.get("count")) == len(root.findall("gpu"))
+    small = ctypes.create_string_buffer(8)
+    assert lib.lutc_device_info(small, 8, None) == _lib.LUTC_ENOMEM and small.value == b""
