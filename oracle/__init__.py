@@ -1,13 +1,14 @@
-"""CPU oracle of detector LUT generation and LUT-based image correction.
+"""CPU oracle of detector LUT generation, LUT-based image correction and the per-detector fit.
 
 TEST INFRASTRUCTURE ONLY: the plain, slow reference that the CUDA library is
 checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline / reference arm may import it.  It shares no code
 with the CUDA path; the definitions it follows are stated in
-``lutc_oracle.c`` (steps L, P, H, S, C, A there).
+``lutc_oracle.c`` (steps L, P, H, S, C, A there) and ``lsq_oracle.c``
+(steps F1-F4 of the least-squares fit).
 
-The C source is compiled with the host ``gcc`` on first use (or by
-:func:`build`) into ``oracle/_build/liblutc_oracle.so``.
+The C sources are compiled with the host ``gcc`` on first use (or by
+:func:`build` and :func:`build_lsq`) into ``oracle/_build/``.
 """
 from __future__ import annotations
 
@@ -170,3 +171,57 @@ def correct_image(raster: np.ndarray, A, G, O, bits: int, stretch: bool = True, 
     if with_tables:
         return out, (hist_, S, lohi)
     return out
+
+
+# ----------------------------------------------------------------------------- least-squares fit (lsq_oracle.c)
+
+_LSQ_SRC = os.path.join(_HERE, "lsq_oracle.c")
+_LSQ_LIB = os.path.join(_HERE, "_build", "liblsq_oracle.so")
+_lsq = None
+
+
+def build_lsq(force: bool = False) -> str:
+    """Compile the fit oracle (host gcc, -O2, no fused multiply-add)."""
+    if force or not os.path.exists(_LSQ_LIB) or os.path.getmtime(_LSQ_LIB) < os.path.getmtime(_LSQ_SRC):
+        os.makedirs(os.path.dirname(_LSQ_LIB), exist_ok=True)
+        tmp = _LSQ_LIB + ".%d.tmp" % os.getpid()
+        subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", _LSQ_SRC, "-o", tmp,
+                        "-lm"], check=True)
+        os.replace(tmp, _LSQ_LIB)
+    return _LSQ_LIB
+
+
+def _load_lsq():
+    global _lsq
+    if _lsq is None:
+        lib = ctypes.CDLL(build_lsq())
+        i32, i64, p = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+        lib.oracle_polyfit.argtypes = [p, i64, p, i64, i32, i32, i32, p, p, p]
+        lib.oracle_polyfit.restype = None
+        _lsq = lib
+    return _lsq
+
+
+def polyfit(x, y, order: int, q16: bool = False):
+    """Per-column least-squares fit of order 1-3 (steps F1-F4 of lsq_oracle.c).
+
+    x: ``[n, ncols]`` uint16 (contiguous rows); y: ``[n, ncols]`` float64, or ``[n]`` (one target
+    per line).  Returns ``(coef [ncols, order+1] float64, status [ncols] int32)`` and, with
+    ``q16``, also ``[3, ncols]`` int32 codes (A, G, O).
+    """
+    x = _c(x, np.uint16)
+    y = _c(y, np.float64)
+    n, ncols, xp = _rows(x)
+    if y.ndim == 1:
+        assert y.shape[0] == n and y.strides[0] == 8
+        yp = 0
+    else:
+        assert y.shape == (n, ncols)
+        _, _, yp = _rows(y)
+    assert 1 <= order <= 3 and not (q16 and order > 2)
+    coef = np.empty((ncols, order + 1), np.float64)
+    status = np.empty(ncols, np.int32)
+    codes = np.empty((3, ncols), np.int32) if q16 else None
+    _load_lsq().oracle_polyfit(x.ctypes.data, xp, y.ctypes.data, yp, n, ncols, order, coef.ctypes.data,
+                               status.ctypes.data, codes.ctypes.data if q16 else None)
+    return (coef, status, codes) if q16 else (coef, status)

@@ -47,6 +47,8 @@ def _load():
         lib.synth_coeffs.argtypes = [u64, i32, i32, p, p, p]
         lib.synth_coeffs.restype = None
         lib.synth_batch_spec.argtypes = [u64, i32, p, p, p, p]
+        lib.synth_calib.argtypes = [u64, i32, i32, i32, f64, p, ctypes.c_int64, p]
+        lib.synth_calib.restype = None
         lib.synth_batch_spec.restype = None
         _lib = lib
     return _lib
@@ -166,3 +168,14 @@ def batch_images(seed: int = BATCH_SEED, n: int = BATCH_IMAGES, nthreads: int = 
         A, G, O = coeff_set(s, bands, W)
         out.append(dict(raw=raw, A=A, G=G, O=O, width=W, height=H, bits=bits, bands=bands))
     return out
+
+
+CALIB_SEED = 1510
+
+
+def calib(seed: int, n: int, width: int, bits: int, *, dead_frac: float = 0.0):
+    """Flat-field calibration scan lines: ``(x [n, width] uint16, y [n] float64 levels)``."""
+    x = np.empty((n, width), np.uint16)
+    y = np.empty(n, np.float64)
+    _load().synth_calib(seed, n, width, bits, dead_frac, x.ctypes.data, width, y.ctypes.data)
+    return x, y

@@ -38,7 +38,8 @@ enum {
     K_GAIN = 6,
     K_OFFS = 7,
     K_QUAD = 8,
-    K_BATCH = 9    /* image specification of a batch (band argument = 0) */
+    K_BATCH = 9,   /* image specification of a batch (band argument = 0) */
+    K_CAL = 10     /* calibration scan lines: per-column response and per-sample noise */
 };
 
 static inline uint64_t mix64(uint64_t z)
@@ -234,5 +235,42 @@ void synth_batch_spec(uint64_t seed, int n, int32_t* width, int32_t* height, int
         int kn = (int)(3.0 * synth_u01(seed, K_BATCH, b + 3));
         bits[i] = bit_set[kb > 2 ? 2 : kb];
         bands[i] = band_set[kn > 2 ? 2 : kn];
+    }
+}
+
+/*
+ * Flat-field calibration scan lines for the per-detector polynomial fit.
+ * Line i (0 <= i < n) images a uniform target of level
+ *     L_i = M * (0.05 + 0.9 * (i + 0.5) / n),  M = 2^bits - 1,
+ * and detector c reads x = clamp(round(b_c + h_c L_i + q_c L_i^2 + e), 0, M)
+ * with gain h_c ~ U(0.9, 1.1), offset b_c ~ U(-20, 20), curvature
+ * q_c ~ U(-2e-5, 2e-5) (scaled by 2^(12 - bits) so that its effect at full
+ * scale is the same at every bit depth) and e ~ N(0, 2) per sample.  A
+ * fraction dead_frac of the columns read 0 on every line.  x is [n][pitch]
+ * uint16, y receives the n levels.
+ */
+void synth_calib(uint64_t seed, int n, int width, int bits, double dead_frac, uint16_t* x, int64_t pitch, double* y)
+{
+    const double M = (double)((1u << bits) - 1u);
+    const double qscale = ldexp(1.0, 12 - bits);
+    for (int i = 0; i < n; ++i) y[i] = M * (0.05 + 0.9 * (i + 0.5) / n);
+    for (int c = 0; c < width; ++c) {
+        const uint64_t st = sid(0, K_CAL);
+        const double h = 0.9 + 0.2 * synth_u01(seed, st, 4 * (uint64_t)c + 0);
+        const double b = -20.0 + 40.0 * synth_u01(seed, st, 4 * (uint64_t)c + 1);
+        const double q = (-2e-5 + 4e-5 * synth_u01(seed, st, 4 * (uint64_t)c + 2)) * qscale;
+        const int dead = synth_u01(seed, st, 4 * (uint64_t)c + 3) < dead_frac;
+        for (int i = 0; i < n; ++i) {
+            uint16_t v = 0;
+            if (!dead) {
+                const uint64_t k = 2 * ((uint64_t)i * (uint64_t)width + (uint64_t)c);
+                const double u1 = synth_u01(seed, sid(1, K_CAL), k);
+                const double u2 = synth_u01(seed, sid(1, K_CAL), k + 1);
+                const double e = 2.0 * sqrt(-2.0 * log(1.0 - u1)) * cos(SYNTH_TWO_PI * u2);
+                double r = llround(b + h * y[i] + q * y[i] * y[i] + e);
+                v = (uint16_t)(r < 0 ? 0 : (r > M ? M : r));
+            }
+            x[(int64_t)i * pitch + c] = v;
+        }
     }
 }
