@@ -390,6 +390,7 @@ def run_lutc(args, wl):
                                              "mean_batch": d["mean_batch"]} for r, d in v["latency"].items()},
                           "outputs_equal_single_calls": v["outputs_equal_single_calls"],
                           "config": v["config"]["workload"]}
+        line["fit"] = run_fit(sub)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -665,6 +666,99 @@ def run_serve(args):
         print(json.dumps(line), flush=True)
 
 
+def fp64_peak_tflops(device) -> tuple[float, str]:
+    """fp64 FMA-pipe peak: SMs x 2 fp64 FMA per clock x 2 flops x maximum SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mhz = 2070.0
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits",
+                              "-i", str(device.index or 0)], capture_output=True, text=True, timeout=20).stdout
+        mhz = float(out.strip().splitlines()[0])
+    except Exception:
+        pass
+    return sms * 2 * 2 * mhz * 1e6 / 1e12, "%d SMs x 2 fp64 FMA/clk x 2 flop x %.0f MHz" % (sms, mhz)
+
+
+def run_fit(args):
+    """Per-detector least-squares fit: the paper's shape (6 lines x 6000 detectors) and a large calibration."""
+    import torch
+    import synth
+    import paper_1505_05655_gb300 as lutc
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(device)
+    peak, peak_how = fp64_peak_tflops(device)
+
+    def timed(fn, steps):
+        torch.cuda.synchronize(device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        return e0.elapsed_time(e1) / steps
+
+    shapes = {"paper": (6, 6000, 12), "large": (1024, 65536, 14)}
+    res = {}
+    for name, (n, ncols, bits) in shapes.items():
+        x, y = synth.calib(synth.CALIB_SEED + rank, n, ncols, bits, dead_frac=0.01)
+        xd, yd = torch.from_numpy(x).to(device), torch.from_numpy(y).to(device)
+        per = {}
+        for order in (1, 2, 3):
+            coef = torch.empty((ncols, order + 1), dtype=torch.float64, device=device)
+            st = torch.empty(ncols, dtype=torch.int32, device=device)
+            call = lambda: lutc.fit(xd, yd, order, coef=coef, status=st, stream=stream)
+            for _ in range(5):
+                call()
+            steps = 200 if name == "paper" else 20
+            ms = timed(call, steps)
+            # kernel time without host overhead: many calls captured in one graph, replayed
+            per_graph = 100 if name == "paper" else 5
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                cs = torch.cuda.current_stream(device)
+                for _ in range(per_graph):
+                    lutc.fit(xd, yd, order, coef=coef, status=st, stream=cs)
+            graph.replay()
+            reps = 10 if name == "paper" else 4
+            gms = timed(graph.replay, reps) / per_graph
+            # fp64 work the method cannot avoid: the moments Q_j = sum x^j y (one multiply-add per j);
+            # the power sums P_k are exact integer sums.  Issued fp64 instructions per sample: one
+            # conversion of x, m - 1 products x^j, m + 1 moment updates.
+            flops = n * ncols * 2 * (order + 1)
+            issue = n * ncols * (2 * order + 1)
+            per[str(order)] = {"us_per_kernel": gms * 1e3, "us_per_call_from_python": ms * 1e3,
+                               "detectors_per_s": ncols / (gms * 1e-3),
+                               "roofline": {"bound": "alu", "achieved": flops / (gms * 1e-3) / 1e12, "peak": peak,
+                                            "unit": "TFLOP/s (fp64)", "frac": flops / (gms * 1e-3) / 1e12 / peak,
+                                            "flops_per_sample": 2 * (order + 1), "peak_source": peak_how,
+                                            "fp64_issue_frac": issue / (gms * 1e-3) / 1e12 / (peak / 2)}}
+            if name == "paper" and rank == 0 and not args.no_cpu_baseline:
+                import oracle
+                t = time.perf_counter()
+                reps = 0
+                while time.perf_counter() - t < 0.5:
+                    rc, rs = oracle.polyfit(x, y, order)
+                    reps += 1
+                dt = (time.perf_counter() - t) / reps
+                same_status = bool(np.array_equal(rs, st.cpu().numpy()))
+                ok = rs == 0
+                sc = float(1 << bits) ** np.arange(order + 1)
+                rel = np.abs(coef.cpu().numpy()[ok] - rc[ok]) * sc / np.maximum(np.abs(rc[ok] * sc).max(axis=1,
+                                                                                                    keepdims=True), 1)
+                per[str(order)]["cpu_baseline"] = {"us_per_call": dt * 1e6, "cores": 1, "kind": "oracle",
+                                                   "sample": "the whole %d x %d calibration" % (n, ncols)}
+                per[str(order)]["parity"] = {"status_equal": same_status,
+                                             "max_rel_diff_scaled_coef": float(rel.max()) if rel.size else 0.0}
+        res[name] = {"lines": n, "detectors": ncols, "bits": bits, "orders": per,
+                     "x_bytes": n * ncols * 2}
+    return res
+
+
 def main():
     import synth
     ap = argparse.ArgumentParser()
@@ -672,7 +766,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="lutc", choices=["lutc", "reference"])
-    ap.add_argument("--workload", default="scene", choices=sorted(synth.WORKLOADS) + ["batch", "serve"])
+    ap.add_argument("--workload", default="scene", choices=sorted(synth.WORKLOADS) + ["batch", "serve", "fit"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--batch-images", type=int, default=256, help="images in the batch workload")
@@ -684,6 +778,9 @@ def main():
         return
     if args.workload == "serve" and args.impl != "reference":
         run_serve(args)
+        return
+    if args.workload == "fit" and args.impl != "reference":
+        print(json.dumps({"workload": "fit", "fit": run_fit(args)}), flush=True)
         return
     wl = synth.WORKLOADS[args.workload if args.workload in synth.WORKLOADS else "scene"]
     if args.impl == "reference":

@@ -235,6 +235,44 @@ LUTC_API int lutc_submit(int task, const char* params, const void* const* inputs
 LUTC_API int lutc_device_info(char* xml, size_t capacity, size_t* needed);
 
 /* ------------------------------------------------------------------------
+ * Per-detector least-squares polynomial fit (Section III.B, case study 2):
+ * the calibration step that produces the coefficients the LUT is built from.
+ * ------------------------------------------------------------------------ */
+
+#define LUTC_FIT_MAX_ORDER 3
+#define LUTC_FIT_MAX_LINES 65536 /**< the exact 64-bit power sums of x^3 hold up to 2^16 lines */
+
+/**
+ * For every column c < ncols, the polynomial f_c(x) = a_0 + a_1 x + ... +
+ * a_m x^m of order m = `order` (1..3) that minimises
+ * sum_{i<n} (y_i - f_c(x[i][c]))^2, by the normal equations the paper
+ * derives (zero first derivatives of the squared error), solved in fp64.
+ *
+ * x: device uint16, n calibration lines of ncols samples, line i at byte
+ *    offset i * x_pitch_bytes (>= 2 * ncols, even).
+ * y: device doubles: with y_pitch_bytes == 0, one target per line (y[i]);
+ *    otherwise one per sample, line i at byte offset i * y_pitch_bytes
+ *    (>= 8 * ncols, multiple of 8).
+ * coef: device double[ncols][order + 1], a_0 first.
+ * status: device int32[ncols]: 0 fitted; 1 fewer than order + 1 distinct
+ *    abscissae in the column (singular system; coefficients NaN, codes 0);
+ *    2 a Q16 code out of range (codes 0).
+ * q16: NULL, or (order <= 2) device int32[3][ncols]: the rows A, G, O of the
+ *    Q16 coefficients of D(x) = A x^2 + G x + O that lutc_lutgen consumes,
+ *    round(a_2 2^16), round(a_1 2^16), round(a_0 2^16) (half away from zero;
+ *    A = 0 for order 1); a code of magnitude above 2^31 - 1 sets status 2.
+ * Returns LUTC_EINVAL (order outside 1..3, n < order + 1 or above
+ * LUTC_FIT_MAX_LINES, q16 with order 3,
+ * null or misaligned buffers, bad pitches) before any launch; ncols == 0
+ * returns LUTC_OK with nothing launched.  Asynchronous on `stream`.
+ * Accuracy: the normal equations square the conditioning of the samples'
+ * Vandermonde matrix; columns whose abscissae span a narrow range lose
+ * digits accordingly (a property of the method, not of the kernel).
+ */
+LUTC_API int lutc_fit(const uint16_t* x, int64_t x_pitch_bytes, const double* y, int64_t y_pitch_bytes, int n,
+                      int ncols, int order, double* coef, int32_t* status, int32_t* q16, lutc_stream stream);
+
+/* ------------------------------------------------------------------------
  * Batches: many independent rasters corrected by one persistent launch per
  * phase.  The paper's server receives tasks from many clients (Sections I-II);
  * a batch is a set of such tasks of uneven size, bit depth and band count,

@@ -19,7 +19,7 @@ from ._lib import (LUTC_MAX_BANDS, LUTC_STRETCH, Coeffs, LutcError, Raster, chec
 __all__ = ["LutcError", "lib", "version", "lutgen", "apply_u16", "hist", "stretch", "compose", "apply_u8",
            "correct_image_workspace", "correct_image_tables", "correct_image", "apply_stretch", "trace_enable",
            "trace_read", "raster_desc", "coeff_descs", "set_tuning", "reset_tuning", "get_tuning", "Batch",
-           "batch_autotune", "Server", "submit",
+           "batch_autotune", "Server", "submit", "fit",
            "device_info"]
 
 
@@ -438,3 +438,36 @@ def device_info() -> str:
     buf = ctypes.create_string_buffer(need.value)
     check(lib().lutc_device_info(buf, need.value, ctypes.byref(need)), "lutc_device_info")
     return buf.value.decode()
+
+
+def fit(x: torch.Tensor, y: torch.Tensor, order: int, q16: bool = False, coef: torch.Tensor | None = None,
+        status: torch.Tensor | None = None, codes: torch.Tensor | None = None, stream=None):
+    """Per-column least-squares polynomial fit of order 1-3 (Section III.B).
+
+    x: ``[n, ncols]`` uint16 on the device (rows may be padded); y: ``[n]`` (one target per
+    line) or ``[n, ncols]`` float64.  Returns ``(coef [ncols, order+1] float64, status [ncols]
+    int32)`` and, with ``q16``, the ``[3, ncols]`` int32 rows A, G, O for :func:`lutgen`.
+    """
+    _need(x, torch.uint16, "x")
+    _need(y, torch.float64, "y")
+    if x.dim() != 2 or (x.numel() and x.stride(1) != 1):
+        raise ValueError("x must be [n, ncols] with contiguous rows")
+    n, ncols = x.shape
+    if y.dim() == 1:
+        if y.shape[0] != n or (n and y.stride(0) != 1):
+            raise ValueError("y must hold one contiguous target per line")
+        y_pitch = 0
+    else:
+        if tuple(y.shape) != (n, ncols) or (y.numel() and y.stride(1) != 1):
+            raise ValueError("y must be [n, ncols] with contiguous rows")
+        y_pitch = y.stride(0) * 8
+    dev = x.device
+    if coef is None:
+        coef = torch.empty((ncols, order + 1), dtype=torch.float64, device=dev)
+    if status is None:
+        status = torch.empty(ncols, dtype=torch.int32, device=dev)
+    if q16 and codes is None:
+        codes = torch.empty((3, ncols), dtype=torch.int32, device=dev)
+    check(lib().lutc_fit(x.data_ptr(), x.stride(0) * 2, y.data_ptr(), y_pitch, n, ncols, order, coef.data_ptr(),
+                         status.data_ptr(), codes.data_ptr() if q16 else None, _stream(stream, dev)), "lutc_fit")
+    return (coef, status, codes) if q16 else (coef, status)

@@ -99,6 +99,7 @@ SIGNATURES = {
     "lutc_set_tuning": (_I, [_I, ctypes.POINTER(Tuning)]),
     "lutc_submit": (_I, [_I, ctypes.c_char_p, ctypes.POINTER(_P), _I, ctypes.POINTER(_P), _I, _P, _SZ, _P]),
     "lutc_device_info": (_I, [ctypes.c_char_p, _SZ, ctypes.POINTER(_SZ)]),
+    "lutc_fit": (_I, [_P, _I64, _P, _I64, _I, _I, _I, _P, _P, _P, _P]),
     "lutc_batch_workspace": (_SZ, [ctypes.POINTER(Job), _I]),
     "lutc_server_create": (_I, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]),
     "lutc_server_register_sensor": (_I, [_P, _I, _I, _I, _I, _P, _P, _P]),

@@ -142,3 +142,17 @@ def test_device_info_document_is_well_formed():
     assert root.tag == "gpus" and int(root.get("count")) == len(root.findall("gpu"))
     small = ctypes.create_string_buffer(8)
     assert lib.lutc_device_info(small, 8, None) == _lib.LUTC_ENOMEM and small.value == b""
+
+
+def test_fit_arguments_are_rejected_before_launch():
+    lib = _lib.lib()
+    E = _lib.LUTC_EINVAL
+    x, y, coef, st, q = 0x10000, 0x20000, 0x30000, 0x40000, 0x50000
+    ok = lambda **kw: dict(dict(x=x, xp=200, y=y, yp=0, n=6, ncols=100, order=2, coef=coef, st=st, q=q), **kw)
+    call = lambda a: lib.lutc_fit(a["x"], a["xp"], a["y"], a["yp"], a["n"], a["ncols"], a["order"], a["coef"],
+                                  a["st"], a["q"], None)
+    for bad in (dict(order=0), dict(order=4), dict(n=2), dict(n=65537), dict(order=3, n=6), dict(xp=198), dict(xp=201),
+                dict(yp=792), dict(yp=804), dict(x=0), dict(y=0), dict(coef=0), dict(st=0), dict(x=0x10001),
+                dict(y=0x20004), dict(ncols=-1)):
+        assert call(ok(**bad)) == E, bad
+    assert call(ok(ncols=0)) == 0  # nothing to fit, nothing launched
