@@ -1,14 +1,15 @@
-"""CPU oracle of detector LUT generation, LUT-based image correction and the per-detector fit.
+"""CPU oracle of detector LUT generation, LUT-based image correction, the per-detector fit and demosaicing.
 
 TEST INFRASTRUCTURE ONLY: the plain, slow reference that the CUDA library is
 checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline / reference arm may import it.  It shares no code
 with the CUDA path; the definitions it follows are stated in
-``lutc_oracle.c`` (steps L, P, H, S, C, A there) and ``lsq_oracle.c``
-(steps F1-F4 of the least-squares fit).
+``lutc_oracle.c`` (steps L, P, H, S, C, A there), ``lsq_oracle.c``
+(steps F1-F4 of the least-squares fit) and ``bayer_oracle.c`` (bilinear
+demosaicing).
 
 The C sources are compiled with the host ``gcc`` on first use (or by
-:func:`build` and :func:`build_lsq`) into ``oracle/_build/``.
+:func:`build`, :func:`build_lsq` and :func:`build_bayer`) into ``oracle/_build/``.
 """
 from __future__ import annotations
 
@@ -225,3 +226,50 @@ def polyfit(x, y, order: int, q16: bool = False):
     _load_lsq().oracle_polyfit(x.ctypes.data, xp, y.ctypes.data, yp, n, ncols, order, coef.ctypes.data,
                                status.ctypes.data, codes.ctypes.data if q16 else None)
     return (coef, status, codes) if q16 else (coef, status)
+
+
+# ----------------------------------------------------------------------------- bilinear demosaic (bayer_oracle.c)
+
+_BAYER_SRC = os.path.join(_HERE, "bayer_oracle.c")
+_BAYER_LIB = os.path.join(_HERE, "_build", "libbayer_oracle.so")
+_bayer = None
+PATTERNS = {"rggb": 0, "bggr": 1, "grbg": 2, "gbrg": 3}
+
+
+def build_bayer(force: bool = False) -> str:
+    """Compile the demosaic oracle (host gcc, -O2)."""
+    if force or not os.path.exists(_BAYER_LIB) or os.path.getmtime(_BAYER_LIB) < os.path.getmtime(_BAYER_SRC):
+        os.makedirs(os.path.dirname(_BAYER_LIB), exist_ok=True)
+        tmp = _BAYER_LIB + ".%d.tmp" % os.getpid()
+        subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _BAYER_SRC, "-o", tmp], check=True)
+        os.replace(tmp, _BAYER_LIB)
+    return _BAYER_LIB
+
+
+def _load_bayer():
+    global _bayer
+    if _bayer is None:
+        lib = ctypes.CDLL(build_bayer())
+        i32, i64, p = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+        lib.oracle_demosaic.argtypes = [p, i64, i32, i32, i32, p, i32, p, i64]
+        lib.oracle_demosaic.restype = None
+        _bayer = lib
+    return _bayer
+
+
+def demosaic(img: np.ndarray, pattern: str = "rggb", lut: np.ndarray | None = None, bits: int = 16) -> np.ndarray:
+    """Bilinear demosaic of one CFA raster (definition in bayer_oracle.c): ``[3, H, W]`` uint16 R, G, B.
+
+    With ``lut`` (``[W, 2^bits]`` uint16, e.g. from :func:`lutgen`) every value is corrected first.
+    """
+    img = _c(img, np.uint16)
+    if img.size == 0:
+        return np.zeros((3,) + img.shape, np.uint16)
+    h, w, pitch = _rows(img)
+    out = np.empty((3, h, w), np.uint16)
+    if lut is not None:
+        lut = np.ascontiguousarray(_c(lut, np.uint16))
+        assert lut.shape == (w, 1 << bits)
+    _load_bayer().oracle_demosaic(img.ctypes.data, pitch, w, h, PATTERNS[pattern],
+                                  lut.ctypes.data if lut is not None else None, bits, out.ctypes.data, max(w, 1))
+    return out

@@ -136,8 +136,9 @@ __global__ void __launch_bounds__(64) k_fit(const uint16_t* __restrict__ x, int6
 #pragma unroll
         for (int k = 0; k < D; ++k) a[k] = __longlong_as_double(0x7ff8000000000000LL);  // quiet NaN
     } else {
-        // Cholesky: normal matrix N[j][k] = P[j+k] = L L^T, lower triangle in L
-        double L[D][D];
+        // Cholesky: normal matrix N[j][k] = P[j+k] = L L^T, lower triangle in L; rinv[k] = 1 / L[k][k]
+        // from one reciprocal square root per pivot, so the solve needs no division
+        double L[D][D], rinv[D];
 #pragma unroll
         for (int j = 0; j < D; ++j) {
 #pragma unroll
@@ -145,7 +146,12 @@ __global__ void __launch_bounds__(64) k_fit(const uint16_t* __restrict__ x, int6
                 double s = P[j + k];
 #pragma unroll
                 for (int t = 0; t < k; ++t) s -= L[j][t] * L[k][t];
-                L[j][k] = (j == k) ? sqrt(s) : s / L[k][k];
+                if (j == k) {
+                    rinv[j] = rsqrt(s);
+                    L[j][j] = s * rinv[j];
+                } else {
+                    L[j][k] = s * rinv[k];
+                }
             }
         }
         double z[D];
@@ -154,14 +160,14 @@ __global__ void __launch_bounds__(64) k_fit(const uint16_t* __restrict__ x, int6
             double s = Q[j];
 #pragma unroll
             for (int t = 0; t < j; ++t) s -= L[j][t] * z[t];
-            z[j] = s / L[j][j];
+            z[j] = s * rinv[j];
         }
 #pragma unroll
         for (int j = D - 1; j >= 0; --j) {
             double s = z[j];
 #pragma unroll
             for (int t = j + 1; t < D; ++t) s -= L[t][j] * a[t];
-            a[j] = s / L[j][j];
+            a[j] = s * rinv[j];
         }
     }
 #pragma unroll
