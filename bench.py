@@ -391,6 +391,7 @@ def run_lutc(args, wl):
                           "outputs_equal_single_calls": v["outputs_equal_single_calls"],
                           "config": v["config"]["workload"]}
         line["fit"] = run_fit(sub)
+        line["demosaic"] = run_demosaic(sub)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -792,6 +793,76 @@ def run_fit(args):
     return res
 
 
+def run_demosaic(args):
+    """Bilinear demosaic: the paper's 2048 x 2048 16-bit frame, and a frame larger than L2, raw and
+    fused with the detector correction."""
+    import torch
+    import synth
+    import paper_1505_05655_gb300 as lutc
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(device)
+    peak, peak_src = peaks()
+
+    def timed(fn, steps):
+        torch.cuda.synchronize(device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        return e0.elapsed_time(e1) / steps
+
+    cases = [("paper 2048x2048 16-bit, raw", 2048, 2048, 16, False),
+             ("paper 2048x2048 12-bit, fused detector correction", 2048, 2048, 12, True),
+             ("large 16384x16384 16-bit, raw", 16384, 16384, 16, False),
+             ("large 16384x16384 12-bit, fused detector correction", 16384, 16384, 12, True)]
+    res = {}
+    for name, h, w, bits, correct in cases:
+        img = synth.raster(synth.CALIB_SEED + 7 + rank, 1, h, w, bits)[0]
+        raw = torch.from_numpy(img).to(device)
+        kw = {}
+        if correct:
+            A, G, O = synth.coeffs(synth.CALIB_SEED + 7 + rank, 0, w)
+            kw = {k: torch.from_numpy(v).to(device) for k, v in (("A", A), ("G", G), ("O", O))}
+        out = torch.empty((3, h, w), dtype=torch.uint16, device=device)
+        call = lambda: lutc.demosaic(raw, "rggb", bits, out=out, stream=stream, **kw)
+        for _ in range(3):
+            call()
+        per_graph = 50 if h <= 2048 else 5
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            cs = torch.cuda.current_stream(device)
+            for _ in range(per_graph):
+                lutc.demosaic(raw, "rggb", bits, out=out, stream=cs, **kw)
+        graph.replay()
+        ms = timed(graph.replay, 10) / per_graph
+        px = h * w
+        alg = 8 * px
+        ach = alg / (ms * 1e-3) / 1e9
+        entry = {"us_per_frame": ms * 1e3, "gpx_s": px / (ms * 1e-3) / 1e9,
+                 "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                              "alg_bytes_per_px": 8, "peak_source": peak_src + " (copy bandwidth)"},
+                 "l2": "frame %s L2 (%.0f MB in, %.0f MB out)" % ("inside" if 8 * px < 129e6 else "larger than",
+                                                                  2 * px / 1e6, 6 * px / 1e6)}
+        if h <= 2048 and rank == 0 and not args.no_cpu_baseline:
+            import oracle
+            lut = oracle.lutgen(A, G, O, bits) if correct else None
+            t = time.perf_counter()
+            ref = oracle.demosaic(img, "rggb", lut=lut, bits=bits)
+            dt = time.perf_counter() - t
+            entry["cpu_baseline"] = {"value": px / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                     "sample": "the whole frame, single-threaded C oracle, %.2f s" % dt}
+            entry["bit_exact_vs_oracle"] = bool(np.array_equal(ref, out.cpu().numpy()))
+        res[name] = entry
+        del raw, out, kw
+        torch.cuda.empty_cache()
+    return res
+
+
 def main():
     import synth
     ap = argparse.ArgumentParser()
@@ -799,7 +870,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="lutc", choices=["lutc", "reference"])
-    ap.add_argument("--workload", default="scene", choices=sorted(synth.WORKLOADS) + ["batch", "serve", "fit"])
+    ap.add_argument("--workload", default="scene", choices=sorted(synth.WORKLOADS) + ["batch", "serve", "fit", "demosaic"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--batch-images", type=int, default=256, help="images in the batch workload")
@@ -811,6 +882,9 @@ def main():
         return
     if args.workload == "serve" and args.impl != "reference":
         run_serve(args)
+        return
+    if args.workload == "demosaic" and args.impl != "reference":
+        print(json.dumps({"workload": "demosaic", "demosaic": run_demosaic(args)}), flush=True)
         return
     if args.workload == "fit" and args.impl != "reference":
         print(json.dumps({"workload": "fit", "fit": run_fit(args)}), flush=True)

@@ -201,7 +201,8 @@ enum {
     LUTC_TASK_COMPOSE = 4,       /**< in {lut, S}; out {clut}; params width, bits */
     LUTC_TASK_APPLY = 5,         /**< in {raster, table}; out {out}; params width, height, bands, bits, table=u16|u8[, pitch, out_pitch] */
     LUTC_TASK_CORRECT_IMAGE = 6, /**< in {raster, A, G, O}; out {out}; params width, height, bands, bits[, stretch, pitch, out_pitch]; workspace */
-    LUTC_TASK_DEVICE_INFO = 7    /**< out {char buffer} (HOST); params capacity */
+    LUTC_TASK_DEVICE_INFO = 7,   /**< out {char buffer} (HOST); params capacity */
+    LUTC_TASK_DEMOSAIC = 8       /**< in {raster[, A, G, O]}; out {rgb}; params width, height, bits, pattern=rggb|bggr|grbg|gbrg[, pitch, out_pitch] */
 };
 
 #define LUTC_PARAMS_MAX 200 /**< longest parameter string (the paper's 200-byte header field) */
@@ -233,6 +234,36 @@ LUTC_API int lutc_submit(int task, const char* params, const void* const* inputs
  * document lists none.
  */
 LUTC_API int lutc_device_info(char* xml, size_t capacity, size_t* needed);
+
+/* ------------------------------------------------------------------------
+ * Bilinear Bayer demosaicing (Section III.A, case study 1), optionally fused
+ * with the detector correction.
+ * ------------------------------------------------------------------------ */
+
+/** Colour filter array patterns, named by the 2x2 cell read row by row from the raster's origin. */
+enum { LUTC_BAYER_RGGB = 0, LUTC_BAYER_BGGR = 1, LUTC_BAYER_GRBG = 2, LUTC_BAYER_GBRG = 3 };
+
+/**
+ * out[k][y][x], k = R, G, B: a pixel keeps its own colour; each missing colour
+ * is the average of the neighbours of that colour among its 8 direct
+ * neighbours inside the image, rounded half up in integers,
+ * (sum + count/2) / count (0 when no such neighbour exists, which happens only
+ * in images one pixel wide or high).  With `coeffs` (one band, ncols == width)
+ * every photosite is first replaced by its detector-corrected value
+ * D[x][min(raw, 2^bits - 1)] (step L), so the interpolation sees corrected
+ * values; without, the raw values are used as they are.
+ *
+ * in: one-band raster (bands == 1); any pitch and alignment, 16-byte aligned
+ *     rows take vector loads.  pattern: LUTC_BAYER_*.
+ * out: device uint16, three planes of in->height rows, plane k row y at byte
+ *     offset (k * height + y) * out_pitch_bytes (>= 2 * width, even); 16-byte
+ *     aligned rows take vector stores.
+ * Returns LUTC_EINVAL for a bad raster, pattern, output or coefficient set
+ * before any launch; an empty raster returns LUTC_OK with nothing launched.
+ * Asynchronous on `stream`.
+ */
+LUTC_API int lutc_demosaic(const lutc_raster* in, const lutc_coeffs* coeffs, int pattern, uint16_t* out,
+                           int64_t out_pitch_bytes, lutc_stream stream);
 
 /* ------------------------------------------------------------------------
  * Per-detector least-squares polynomial fit (Section III.B, case study 2):

@@ -19,7 +19,7 @@ from ._lib import (LUTC_MAX_BANDS, LUTC_STRETCH, Coeffs, LutcError, Raster, chec
 __all__ = ["LutcError", "lib", "version", "lutgen", "apply_u16", "hist", "stretch", "compose", "apply_u8",
            "correct_image_workspace", "correct_image_tables", "correct_image", "apply_stretch", "trace_enable",
            "trace_read", "raster_desc", "coeff_descs", "set_tuning", "reset_tuning", "get_tuning", "Batch",
-           "batch_autotune", "Server", "submit", "fit",
+           "batch_autotune", "Server", "submit", "fit", "demosaic",
            "device_info"]
 
 
@@ -471,3 +471,28 @@ def fit(x: torch.Tensor, y: torch.Tensor, order: int, q16: bool = False, coef: t
     check(lib().lutc_fit(x.data_ptr(), x.stride(0) * 2, y.data_ptr(), y_pitch, n, ncols, order, coef.data_ptr(),
                          status.data_ptr(), codes.data_ptr() if q16 else None, _stream(stream, dev)), "lutc_fit")
     return (coef, status, codes) if q16 else (coef, status)
+
+
+def demosaic(raw: torch.Tensor, pattern: str = "rggb", bits: int = 16, A: torch.Tensor | None = None,
+             G: torch.Tensor | None = None, O: torch.Tensor | None = None, out: torch.Tensor | None = None,
+             stream=None) -> torch.Tensor:
+    """Bilinear Bayer demosaic of a ``[H, W]`` uint16 CFA raster into ``[3, H, W]`` uint16 R, G, B planes
+    (Section III.A); with per-column coefficients ``A, G, O`` (``[W]`` int32) every photosite is
+    detector-corrected first."""
+    from ._lib import LUTC_BAYER
+    desc = raster_desc(raw, bits)
+    if desc.bands != 1:
+        raise ValueError("demosaic takes one CFA band")
+    cd = coeff_descs(A, G, O)[0] if A is not None else None
+    H, W = raw.shape[-2], raw.shape[-1]
+    if out is None:
+        out = torch.empty((3, H, W), dtype=torch.uint16, device=raw.device)
+    _need(out, torch.uint16, "out")
+    if out.dim() != 3 or out.shape[0] != 3 or (out.numel() and (out.stride(2) != 1 or
+                                                                 (H > 0 and out.stride(0) != H * out.stride(1)))):
+        raise ValueError("out must be [3, H, W] with contiguous rows stacked at H * pitch")
+    pitch = out.stride(1) * 2 if out.numel() else 2 * W
+    check(lib().lutc_demosaic(ctypes.byref(desc), ctypes.byref(cd) if cd is not None else None,
+                              LUTC_BAYER[pattern], out.data_ptr(), pitch, _stream(stream, raw.device)),
+          "lutc_demosaic")
+    return out

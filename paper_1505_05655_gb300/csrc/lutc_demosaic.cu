@@ -1,0 +1,278 @@
+// Bilinear Bayer demosaicing (paper, Section III.A, case study 1), optionally
+// fused with the detector correction (step L applied to every photosite first).
+//
+// Definition: a pixel keeps its own colour; each missing colour is the
+// average of the neighbours of that colour among its 8 direct neighbours
+// inside the image, rounded half up in integers, (sum + count/2) / count.
+// For the four sites of a Bayer cell that is: at a red or blue site, green
+// from the 4 orthogonal and the opposite colour from the 4 diagonal
+// neighbours; at a green site, one colour from the left/right pair and the
+// other from the up/down pair.
+//
+// GB300 mapping: a block owns a 128-column tile (16 rows raw, 32 rows with
+// correction; see Tile).  The tile and a halo (one row above and below, one
+// 8-column chunk left and right, so every load is an aligned vector) is staged
+// in shared memory, corrected on the way in when coefficients are given (the
+// int32/int64 Horner evaluation of step L).
+// Each thread then produces a 2 x 8 patch: reads 4 shared rows of 12 values
+// (one 16-byte and two 4-byte loads per row), resolves the Bayer role of each
+// pixel at compile time (pattern phase is a template parameter, patch origins
+// are even), and writes 16-byte vectors to the three planar outputs.  Blocks
+// whose halo lies inside the image take a path with constant neighbour
+// counts; border blocks count the neighbours that exist.  HBM traffic per
+// pixel: 2 bytes in, 6 bytes out (the halo re-reads hit L2).
+#include <stdint.h>
+
+#include "lutc_internal.cuh"
+
+namespace lutc {
+namespace {
+
+// Tile shapes (measured on GB300, 16384 x 16384 frames): the raw path runs
+// 128 x 16 tiles in blocks of 128 threads, 8 blocks per SM; the corrected path
+// runs 128 x 32 tiles in blocks of 256 threads, 4 per SM, whose loaders hold
+// their columns' coefficients in registers.
+template <bool kCorrect>
+struct Tile {
+    static constexpr int W = 128, H = kCorrect ? 32 : 16;
+    static constexpr int threads = (W / 8) * (H / 2);   // one 2 x 8 patch per thread
+    static constexpr int min_blocks = kCorrect ? 4 : 8;
+    static constexpr int SW = W + 16, SH = H + 2;       // staged tile with halo (uint16)
+    static constexpr int chunk = kCorrect ? 4 : 8;      // columns per loader load (8 or 16 bytes)
+    static constexpr int chunks = SW / chunk;           // loads per staged row
+    static constexpr int lanes = threads / chunks;      // row lanes of the loader
+};
+
+struct DemosaicArgs {
+    const uint8_t* in;
+    int64_t in_pitch;
+    int W, H, bits;
+    BandCoef coef;     // A == nullptr: no correction
+    uint8_t* out;
+    int64_t out_pitch;
+    bool vin, vout;    // 16-byte aligned rows in / out
+};
+
+// (sum + cnt/2) / cnt for cnt in 0..4 and sum < 2^18, exactly: multiply by ceil(2^20 / cnt)
+__device__ __forceinline__ uint32_t avg_n(uint32_t sum, uint32_t cnt)
+{
+    const uint32_t mul = cnt == 0 ? 0u : cnt == 1 ? (1u << 20) : cnt == 2 ? (1u << 19) : cnt == 3 ? 349526u : (1u << 18);
+    return (uint32_t)(((uint64_t)(sum + (cnt >> 1)) * mul) >> 20);
+}
+
+// Stages rows y0-1 .. y0+H and columns x0-8 .. x0+W+7 of the raw frame (zero
+// outside it), corrected when kCorrect: a loader thread owns `chunk` adjacent
+// staged columns, keeps their coefficients in registers and walks the rows.
+template <bool kCorrect>
+__device__ __forceinline__ void stage_tile(const DemosaicArgs& a, int x0, int y0,
+                                           uint16_t (*s)[Tile<kCorrect>::SW])
+{
+    using T = Tile<kCorrect>;
+    constexpr int CW = T::chunk;
+    const int t = threadIdx.x;
+    if (t >= T::chunks * T::lanes) return;
+    const int ch = t % T::chunks, lane = t / T::chunks;
+    const int gx0 = x0 - 8 + ch * CW;
+    const int32_t M = (1 << a.bits) - 1;
+    int32_t cA[CW], cG[CW], cO[CW];
+    bool fits[CW];
+    if (kCorrect) {
+#pragma unroll
+        for (int j = 0; j < CW; ++j) {
+            const int gx = gx0 + j;
+            const bool in = gx >= 0 && gx < a.W;
+            cA[j] = in ? __ldg(a.coef.A + gx) : 0;
+            cG[j] = in ? __ldg(a.coef.G + gx) : 0;
+            cO[j] = in ? __ldg(a.coef.O + gx) : 0;
+            fits[j] = col_fits_i32(cA[j], cG[j], cO[j], M);
+            if (fits[j]) cO[j] += 32768;
+        }
+    }
+    const bool full = a.vin && gx0 >= 0 && gx0 + CW <= a.W;
+    for (int r = lane; r < T::SH; r += T::lanes) {
+        const int gy = y0 - 1 + r;
+        uint32_t v[CW];
+#pragma unroll
+        for (int j = 0; j < CW; ++j) v[j] = 0;
+        if (gy >= 0 && gy < a.H) {
+            const uint8_t* row = a.in + (int64_t)gy * a.in_pitch + (int64_t)gx0 * 2;
+            if (full) {
+                if constexpr (CW == 8) {
+                    const uint4 q = __ldg(reinterpret_cast<const uint4*>(row));
+                    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                    for (int j = 0; j < CW; ++j) v[j] = (w[j / 2] >> (16 * (j & 1))) & 0xffffu;
+                } else {
+                    const uint2 q = __ldg(reinterpret_cast<const uint2*>(row));
+                    const uint32_t w[2] = {q.x, q.y};
+#pragma unroll
+                    for (int j = 0; j < CW; ++j) v[j] = (w[j / 2] >> (16 * (j & 1))) & 0xffffu;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < CW; ++j) {
+                    const int gx = gx0 + j;
+                    if (gx >= 0 && gx < a.W) v[j] = __ldg(reinterpret_cast<const uint16_t*>(row) + j);
+                }
+            }
+            if (kCorrect) {
+#pragma unroll
+                for (int j = 0; j < CW; ++j) {
+                    const int gx = gx0 + j;
+                    if (gx >= 0 && gx < a.W) {
+                        const uint32_t x = min(v[j], (uint32_t)M);
+                        v[j] = fits[j] ? det_i32(cA[j], cG[j], cO[j], x, M) : det_i64(cA[j], cG[j], cO[j], x, M);
+                    }
+                }
+            }
+        }
+        uint32_t w[CW / 2];
+#pragma unroll
+        for (int j = 0; j < CW / 2; ++j) w[j] = v[2 * j] | (v[2 * j + 1] << 16);
+        if constexpr (CW == 8)
+            *reinterpret_cast<uint4*>(&s[r][ch * CW]) = make_uint4(w[0], w[1], w[2], w[3]);
+        else
+            *reinterpret_cast<uint2*>(&s[r][ch * CW]) = make_uint2(w[0], w[1]);
+    }
+}
+
+// Bayer role of a pixel under RGGB at parity (py, px): 0 R site, 1 G in a red row, 2 G in a blue row, 3 B site
+__host__ __device__ constexpr int role(int py, int px) { return py == 0 ? (px == 0 ? 0 : 1) : (px == 0 ? 2 : 3); }
+
+template <int PY, int PX, bool kCorrect>
+__global__ void __launch_bounds__(Tile<kCorrect>::threads, Tile<kCorrect>::min_blocks) k_demosaic(DemosaicArgs a)
+{
+    using T = Tile<kCorrect>;
+    constexpr int kTW = T::W, kTH = T::H;
+    __shared__ __align__(16) uint16_t s[T::SH][T::SW];
+    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
+    stage_tile<kCorrect>(a, x0, y0, s);
+    __syncthreads();
+
+    const int cx = threadIdx.x % (kTW / 8), ry = threadIdx.x / (kTW / 8);
+    const int c0 = 8 + cx * 8;   // staged column of the patch's first pixel
+    const int r0 = 1 + ry * 2;   // staged row of the patch's first row
+    const int gx = x0 + cx * 8, gy = y0 + ry * 2;
+    if (gx >= a.W || gy >= a.H) return;
+
+    // 4 staged rows x 12 values (columns c0-2 .. c0+9)
+    uint32_t v[4][12];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint16_t* row = s[r0 - 1 + i];
+        const uint32_t lo = *reinterpret_cast<const uint32_t*>(row + c0 - 2);
+        const uint4 mid = *reinterpret_cast<const uint4*>(row + c0);
+        const uint32_t hi = *reinterpret_cast<const uint32_t*>(row + c0 + 8);
+        v[i][0] = lo & 0xffffu; v[i][1] = lo >> 16;
+        v[i][2] = mid.x & 0xffffu; v[i][3] = mid.x >> 16; v[i][4] = mid.y & 0xffffu; v[i][5] = mid.y >> 16;
+        v[i][6] = mid.z & 0xffffu; v[i][7] = mid.z >> 16; v[i][8] = mid.w & 0xffffu; v[i][9] = mid.w >> 16;
+        v[i][10] = hi & 0xffffu; v[i][11] = hi >> 16;
+    }
+
+    // the block's halo is inside the image: every neighbour exists
+    const bool interior = x0 > 0 && y0 > 0 && x0 + kTW < a.W && y0 + kTH < a.H;
+    const bool full = a.vout && gx + 8 <= a.W;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int y = gy + i;
+        if (y >= a.H) break;
+        const uint32_t nu = interior || y > 0, nd = interior || y + 1 < a.H;
+        uint32_t out[3][8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int x = gx + j;
+            const uint32_t nl = interior || x > 0, nr = interior || x + 1 < a.W;
+            const uint32_t c = v[i + 1][j + 2];
+            const uint32_t hs = v[i + 1][j + 1] + v[i + 1][j + 3];
+            const uint32_t vs = v[i][j + 2] + v[i + 2][j + 2];
+            const uint32_t ds = v[i][j + 1] + v[i][j + 3] + v[i + 2][j + 1] + v[i + 2][j + 3];
+            uint32_t orth, diag, horiz, vert;
+            if (interior) {
+                orth = (hs + vs + 2) >> 2;
+                diag = (ds + 2) >> 2;
+                horiz = (hs + 1) >> 1;
+                vert = (vs + 1) >> 1;
+            } else {
+                const uint32_t nh = nl + nr, nv = nu + nd;
+                orth = avg_n(hs + vs, nh + nv);
+                diag = avg_n(ds, nh * nv);
+                horiz = avg_n(hs, nh);
+                vert = avg_n(vs, nv);
+            }
+            switch (role((i + PY) & 1, (j + PX) & 1)) {
+            case 0: out[0][j] = c; out[1][j] = orth; out[2][j] = diag; break;
+            case 1: out[0][j] = horiz; out[1][j] = c; out[2][j] = vert; break;
+            case 2: out[0][j] = vert; out[1][j] = c; out[2][j] = horiz; break;
+            default: out[0][j] = diag; out[1][j] = orth; out[2][j] = c; break;
+            }
+        }
+        // this row of the patch in the three planes
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint16_t* row = reinterpret_cast<uint16_t*>(a.out + ((int64_t)k * a.H + y) * a.out_pitch);
+            if (full) {
+                uint4 q;
+                q.x = out[k][0] | (out[k][1] << 16);
+                q.y = out[k][2] | (out[k][3] << 16);
+                q.z = out[k][4] | (out[k][5] << 16);
+                q.w = out[k][6] | (out[k][7] << 16);
+                *reinterpret_cast<uint4*>(row + gx) = q;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (gx + j < a.W) row[gx + j] = (uint16_t)out[k][j];
+            }
+        }
+    }
+}
+
+template <bool kCorrect>
+void launch(int py, int px, int W, int H, cudaStream_t st, const DemosaicArgs& a)
+{
+    using T = Tile<kCorrect>;
+    const dim3 grid((unsigned)((W + T::W - 1) / T::W), (unsigned)((H + T::H - 1) / T::H));
+    switch (2 * py + px) {
+    case 0: k_demosaic<0, 0, kCorrect><<<grid, T::threads, 0, st>>>(a); break;
+    case 1: k_demosaic<0, 1, kCorrect><<<grid, T::threads, 0, st>>>(a); break;
+    case 2: k_demosaic<1, 0, kCorrect><<<grid, T::threads, 0, st>>>(a); break;
+    default: k_demosaic<1, 1, kCorrect><<<grid, T::threads, 0, st>>>(a); break;
+    }
+}
+
+}  // namespace
+}  // namespace lutc
+
+using namespace lutc;
+
+extern "C" int lutc_demosaic(const lutc_raster* in, const lutc_coeffs* coeffs, int pattern, uint16_t* out,
+                             int64_t out_pitch_bytes, lutc_stream stream)
+{
+    if (!in || in->bands != 1) return LUTC_EINVAL;
+    int rc = check_raster(in);
+    if (rc) return rc;
+    if (pattern < LUTC_BAYER_RGGB || pattern > LUTC_BAYER_GBRG) return LUTC_EINVAL;
+    if ((int64_t)in->width * in->height == 0) return LUTC_OK;
+    if (!out || ((uintptr_t)out % 2) || out_pitch_bytes < 2 * (int64_t)in->width || (out_pitch_bytes % 2))
+        return LUTC_EINVAL;
+    if (coeffs && (!coeffs->A || !coeffs->G || !coeffs->O || coeffs->ncols != in->width)) return LUTC_EINVAL;
+    // pattern -> the row / column shift that turns it into RGGB
+    static const int kPY[4] = {0, 1, 0, 1}, kPX[4] = {0, 1, 1, 0};
+    DemosaicArgs a;
+    a.in = reinterpret_cast<const uint8_t*>(in->data);
+    a.in_pitch = in->pitch_bytes;
+    a.W = in->width;
+    a.H = in->height;
+    a.bits = in->bits;
+    a.coef = coeffs ? BandCoef{coeffs->A, coeffs->G, coeffs->O} : BandCoef{nullptr, nullptr, nullptr};
+    a.out = reinterpret_cast<uint8_t*>(out);
+    a.out_pitch = out_pitch_bytes;
+    a.vin = ((uintptr_t)in->data % 16) == 0 && (in->pitch_bytes % 16) == 0;
+    a.vout = ((uintptr_t)out % 16) == 0 && (out_pitch_bytes % 16) == 0;
+    if ((in->height + 15) / 16 > 65535) return LUTC_EUNSUPPORTED;  // grid rows of the raw path's 16-row tiles
+    cudaStream_t st = (cudaStream_t)stream;
+    if (coeffs)
+        launch<true>(kPY[pattern], kPX[pattern], in->width, in->height, st, a);
+    else
+        launch<false>(kPY[pattern], kPX[pattern], in->width, in->height, st, a);
+    return cuda_status(cudaGetLastError());
+}

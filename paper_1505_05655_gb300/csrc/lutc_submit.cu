@@ -22,6 +22,7 @@ namespace {
 struct Params {
     int64_t width = -1, height = -1, bands = 1, bits = -1, pitch = -1, out_pitch = -1, stretch = 1, capacity = -1;
     int table = 0;  // 0 unset, 1 u16, 2 u8
+    int pattern = -1;
 };
 
 // "key=value,key=value": every key known, every value a non-negative decimal (or u16/u8 for table)
@@ -40,6 +41,14 @@ int parse(const char* text, Params& p)
         const size_t eq = item.find('=');
         if (eq == std::string::npos || eq == 0 || eq + 1 >= item.size()) return LUTC_EINVAL;
         const std::string key = item.substr(0, eq), val = item.substr(eq + 1);
+        if (key == "pattern") {
+            static const char* kNames[4] = {"rggb", "bggr", "grbg", "gbrg"};
+            p.pattern = -1;
+            for (int k = 0; k < 4; ++k)
+                if (val == kNames[k]) p.pattern = k;
+            if (p.pattern < 0) return LUTC_EINVAL;
+            continue;
+        }
         if (key == "table") {
             if (val == "u16") p.table = 1;
             else if (val == "u8") p.table = 2;
@@ -152,6 +161,17 @@ extern "C" int lutc_submit(int task, const char* params, const void* const* in, 
         return lutc_correct_image(&r, c.data(), p.stretch ? LUTC_STRETCH : 0, out[0],
                                   p.out_pitch >= 0 ? p.out_pitch : elem * p.width, workspace, workspace_bytes,
                                   stream);
+    }
+    case LUTC_TASK_DEMOSAIC: {
+        if (!need(p, true, true, true) || p.bands != 1 || p.pattern < 0 || n_in < 1 || n_out < 1) return LUTC_EINVAL;
+        const lutc_raster r = raster_of(p, in[0]);
+        const bool correct = n_in >= 4;
+        const lutc_coeffs c = correct ? lutc_coeffs{reinterpret_cast<const int32_t*>(in[1]),
+                                                    reinterpret_cast<const int32_t*>(in[2]),
+                                                    reinterpret_cast<const int32_t*>(in[3]), (int32_t)p.width}
+                                      : lutc_coeffs{nullptr, nullptr, nullptr, 0};
+        return lutc_demosaic(&r, correct ? &c : nullptr, p.pattern, reinterpret_cast<uint16_t*>(out[0]),
+                             p.out_pitch >= 0 ? p.out_pitch : 2 * p.width, stream);
     }
     case LUTC_TASK_DEVICE_INFO: {
         if (p.capacity < 1 || n_out < 1) return LUTC_EINVAL;

@@ -156,3 +156,25 @@ def test_fit_arguments_are_rejected_before_launch():
                 dict(y=0x20004), dict(ncols=-1)):
         assert call(ok(**bad)) == E, bad
     assert call(ok(ncols=0)) == 0  # nothing to fit, nothing launched
+
+
+def test_demosaic_arguments_are_rejected_before_launch():
+    lib = _lib.lib()
+    E = _lib.LUTC_EINVAL
+    r = _raster()
+    good = Coeffs(0x20000, 0x30000, 0x40000, 100)
+    out = ctypes.c_void_p(0x50000)
+    assert lib.lutc_demosaic(ctypes.byref(r), None, 4, out, 200, None) == E
+    assert lib.lutc_demosaic(ctypes.byref(r), None, -1, out, 200, None) == E
+    assert lib.lutc_demosaic(ctypes.byref(r), None, 0, out, 198, None) == E
+    assert lib.lutc_demosaic(ctypes.byref(r), None, 0, None, 200, None) == E
+    assert lib.lutc_demosaic(ctypes.byref(r), None, 0, ctypes.c_void_p(0x50001), 200, None) == E
+    assert lib.lutc_demosaic(ctypes.byref(_raster(bands=2)), None, 0, out, 200, None) == E
+    assert lib.lutc_demosaic(ctypes.byref(r), ctypes.byref(Coeffs(0x20000, 0x30000, 0x40000, 99)), 0, out, 200,
+                             None) == E
+    assert lib.lutc_demosaic(ctypes.byref(r), ctypes.byref(Coeffs(0, 0x30000, 0x40000, 100)), 0, out, 200, None) == E
+    assert lib.lutc_demosaic(ctypes.byref(_raster(width=0, data=0)), ctypes.byref(good), 0, out, 0, None) == 0
+    bufs = (ctypes.c_void_p * 4)(0x1000, 0x2000, 0x3000, 0x4000)
+    for p in (b"width=100,height=10,bits=12,pattern=rgbg", b"width=100,height=10,bits=12",
+              b"width=100,height=10,bits=12,bands=2,pattern=rggb"):
+        assert lib.lutc_submit(_lib.LUTC_TASK_DEMOSAIC, p, bufs, 1, bufs, 1, None, 0, None) == E
