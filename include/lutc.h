@@ -185,6 +185,38 @@ LUTC_API int lutc_apply_stretch(const lutc_raster* in, const lutc_coeffs* per_ba
  */
 LUTC_API int lutc_device_status(int* status, lutc_stream stream);
 
+/**
+ * Device workspace bytes of lutc_correct_image_host for this raster and flags
+ * (0 for an invalid raster or flags): the fused path's tables, a device copy
+ * of the raster and a staging area for the output (rows padded to 16 bytes).
+ */
+LUTC_API size_t lutc_correct_image_host_workspace(const lutc_raster* in, int flags);
+
+/**
+ * lutc_correct_image for a raster and an output in HOST memory: the same
+ * result, with the host-to-device copies, both passes and the device-to-host
+ * copies pipelined in chunks of rows (copy engines in both directions overlap
+ * each other and the kernels; Section II's client-server round trip, whose
+ * transfer cost the paper's future work sets out to cut).
+ *
+ * in: raster whose `data` is host memory (page-locked memory lets the copies
+ *     run asynchronously and overlap; pageable memory works but serialises).
+ *     Any pitch; layout as for lutc_correct_image.
+ * per_band: device coefficients, as for lutc_correct_image.
+ * out: host memory, uint8 (LUTC_STRETCH) or uint16 rows, band b row y at
+ *     byte offset (b * height + y) * out_pitch_bytes.
+ * workspace: device, >= lutc_correct_image_host_workspace(in, flags) bytes,
+ *     256-byte aligned; caller-owned.
+ * Work runs on `stream` and on two library-owned copy streams per device;
+ * `stream` is made to wait for all of it, so work enqueued on `stream`
+ * afterwards (or a synchronisation of it) sees the finished output.  Returns
+ * LUTC_EINVAL / LUTC_ENOMEM before anything is enqueued, LUTC_ECUDA if an
+ * enqueue fails.
+ */
+LUTC_API int lutc_correct_image_host(const lutc_raster* in, const lutc_coeffs* per_band, int flags, void* out,
+                                     int64_t out_pitch_bytes, void* workspace, size_t workspace_bytes,
+                                     lutc_stream stream);
+
 /* ------------------------------------------------------------------------
  * The paper's task interface.  A client names a task with a flag, passes a
  * comma-separated parameter list of at most 200 bytes (sizes of the data

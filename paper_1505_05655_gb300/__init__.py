@@ -19,7 +19,7 @@ from ._lib import (LUTC_MAX_BANDS, LUTC_STRETCH, Coeffs, LutcError, Raster, chec
 __all__ = ["LutcError", "lib", "version", "lutgen", "apply_u16", "hist", "stretch", "compose", "apply_u8",
            "correct_image_workspace", "correct_image_tables", "correct_image", "apply_stretch", "trace_enable",
            "trace_read", "raster_desc", "coeff_descs", "set_tuning", "reset_tuning", "get_tuning", "Batch",
-           "batch_autotune", "Server", "submit", "fit", "demosaic",
+           "batch_autotune", "Server", "submit", "fit", "demosaic", "correct_image_host",
            "device_info"]
 
 
@@ -495,4 +495,37 @@ def demosaic(raw: torch.Tensor, pattern: str = "rggb", bits: int = 16, A: torch.
     check(lib().lutc_demosaic(ctypes.byref(desc), ctypes.byref(cd) if cd is not None else None,
                               LUTC_BAYER[pattern], out.data_ptr(), pitch, _stream(stream, raw.device)),
           "lutc_demosaic")
+    return out
+
+
+def correct_image_host(raw: torch.Tensor, A: torch.Tensor, G: torch.Tensor, O: torch.Tensor, bits: int,
+                       stretch: bool = True, out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                       stream=None, device=None) -> torch.Tensor:
+    """:func:`correct_image` for a raster in host memory (CPU tensor, ideally pinned), output in host
+    memory; copies and both passes are pipelined in the library.  Synchronises nothing: synchronise
+    ``stream`` (or the device) before reading ``out``."""
+    if raw.device.type != "cpu" or raw.dtype != torch.uint16:
+        raise TypeError("raw must be a host (CPU) torch.uint16 tensor")
+    r3 = raw if raw.dim() == 3 else raw.unsqueeze(0)
+    bands, h, w = r3.shape
+    if r3.numel() and (r3.stride(2) != 1 or (bands > 1 and h > 0 and r3.stride(0) != h * r3.stride(1))):
+        raise ValueError("raw must be [bands, height, width] with contiguous rows stacked at height * pitch")
+    desc = Raster(r3.data_ptr(), (r3.stride(1) if r3.numel() else w) * 2, w, h, bands, bits)
+    cd = coeff_descs(A, G, O)
+    dev = A.device if device is None else torch.device(device)
+    odt = torch.uint8 if stretch else torch.uint16
+    if out is None:
+        out = torch.empty(r3.shape, dtype=odt, pin_memory=raw.is_pinned())
+    if out.device.type != "cpu" or out.dtype != odt:
+        raise TypeError("out must be a host (CPU) %s tensor" % odt)
+    o3 = out if out.dim() == 3 else out.unsqueeze(0)
+    if o3.numel() and (o3.stride(2) != 1 or (bands > 1 and h > 0 and o3.stride(0) != h * o3.stride(1))):
+        raise ValueError("out must be [bands, height, width] with contiguous rows stacked at height * pitch")
+    opitch = (o3.stride(1) if o3.numel() else w) * out.element_size()
+    flags = LUTC_STRETCH if stretch else 0
+    need = int(lib().lutc_correct_image_host_workspace(ctypes.byref(desc), flags))
+    if workspace is None:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    check(lib().lutc_correct_image_host(ctypes.byref(desc), cd, flags, out.data_ptr(), opitch, workspace.data_ptr(),
+                                        workspace.numel(), _stream(stream, dev)), "lutc_correct_image_host")
     return out

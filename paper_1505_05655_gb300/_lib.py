@@ -101,6 +101,8 @@ SIGNATURES = {
     "lutc_submit": (_I, [_I, ctypes.c_char_p, ctypes.POINTER(_P), _I, ctypes.POINTER(_P), _I, _P, _SZ, _P]),
     "lutc_device_info": (_I, [ctypes.c_char_p, _SZ, ctypes.POINTER(_SZ)]),
     "lutc_fit": (_I, [_P, _I64, _P, _I64, _I, _I, _I, _P, _P, _P, _P]),
+    "lutc_correct_image_host_workspace": (_SZ, [ctypes.POINTER(Raster), _I]),
+    "lutc_correct_image_host": (_I, [ctypes.POINTER(Raster), ctypes.POINTER(Coeffs), _I, _P, _I64, _P, _SZ, _P]),
     "lutc_demosaic": (_I, [ctypes.POINTER(Raster), ctypes.POINTER(Coeffs), _I, _P, _I64, _P]),
     "lutc_batch_workspace": (_SZ, [ctypes.POINTER(Job), _I]),
     "lutc_server_create": (_I, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]),

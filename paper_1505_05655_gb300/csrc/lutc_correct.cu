@@ -372,6 +372,35 @@ cudaEvent_t* trace_slot()
     if (g_trace.used >= g_trace.capacity) return nullptr;
     return g_trace.ev + (size_t)(g_trace.used++) * (LUTC_TRACE_PHASES + 1);
 }
+// Pass 1 into an existing histogram (no clear) and pass 2, for the library's own pipelines.
+int pass1_accumulate(const lutc_raster* in, const lutc_coeffs* per_band, unsigned long long* hist, cudaStream_t st)
+{
+    if ((int64_t)in->width * in->height == 0) return LUTC_OK;
+    if (tma_eligible(in)) return tma_hist(in, per_band, hist, st);
+    StripArgs a = make_args(in, per_band);
+    return launch_hist(a, in, hist, st);
+}
+
+int pass2(const lutc_raster* in, const lutc_coeffs* per_band, const uint8_t* S, void* out, int64_t out_pitch,
+          bool stretch, cudaStream_t st)
+{
+    if ((int64_t)in->width * in->height == 0) return LUTC_OK;
+    if (tma_eligible(in)) return tma_apply(in, per_band, S, out, out_pitch, stretch, st);
+    StripArgs a = make_args(in, per_band);
+    return stretch ? launch_apply<true>(a, in, S, out, out_pitch, st)
+                   : launch_apply<false>(a, in, nullptr, out, out_pitch, st);
+}
+
+size_t tables_bytes(const lutc_raster* in) { return layout_of(in).total; }
+
+void tables_offsets(const lutc_raster* in, size_t* hist, size_t* S, size_t* lohi)
+{
+    const Layout l = layout_of(in);
+    *hist = l.hist;
+    *S = l.S;
+    *lohi = l.lohi;
+}
+
 }  // namespace lutc
 
 using namespace lutc;

@@ -108,6 +108,14 @@ enum { kModeHist = 0, kModeHistGlobal = 1, kModeApplyStretch = 2, kModeApplyDete
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Fused-path building blocks (lutc_correct.cu): pass 1 accumulating into a cleared histogram,
+// pass 2 with (S != nullptr, stretch) or without the stretch, and the workspace table layout.
+int pass1_accumulate(const lutc_raster* in, const lutc_coeffs* per_band, unsigned long long* hist, cudaStream_t st);
+int pass2(const lutc_raster* in, const lutc_coeffs* per_band, const uint8_t* S, void* out, int64_t out_pitch,
+          bool stretch, cudaStream_t st);
+size_t tables_bytes(const lutc_raster* in);
+void tables_offsets(const lutc_raster* in, size_t* hist, size_t* S, size_t* lohi);
+
 // returns LUTC_OK or LUTC_EINVAL
 int check_raster(const lutc_raster* r);
 int check_coeff_set(const lutc_raster* r, const lutc_coeffs* per_band);

@@ -178,3 +178,24 @@ def test_demosaic_arguments_are_rejected_before_launch():
     for p in (b"width=100,height=10,bits=12,pattern=rgbg", b"width=100,height=10,bits=12",
               b"width=100,height=10,bits=12,bands=2,pattern=rggb"):
         assert lib.lutc_submit(_lib.LUTC_TASK_DEMOSAIC, p, bufs, 1, bufs, 1, None, 0, None) == E
+
+
+def test_host_path_workspace_and_rejections():
+    lib = _lib.lib()
+    r = _raster(bands=3, width=1000, height=500, pitch_bytes=2002)
+    ws = lib.lutc_correct_image_host_workspace(ctypes.byref(r), 1)
+    # tables + device raster (rows padded to 16 B) + uint8 staging (rows padded to 16 B)
+    assert ws >= lib.lutc_correct_image_workspace(ctypes.byref(r)) + 3 * 500 * 2000 + 3 * 500 * 1008
+    wd = lib.lutc_correct_image_host_workspace(ctypes.byref(r), 0)
+    assert wd >= 3 * 500 * 2000 + 3 * 500 * 2000 and wd < ws + 3 * 500 * 1008
+    assert lib.lutc_correct_image_host_workspace(ctypes.byref(r), 4) == 0
+    assert lib.lutc_correct_image_host_workspace(ctypes.byref(_raster(bits=17)), 1) == 0
+    c = (Coeffs * 3)(*[Coeffs(0x20000, 0x30000, 0x40000, 1000)] * 3)
+    E = _lib.LUTC_EINVAL
+    out, dws = ctypes.c_void_p(0x60000), ctypes.c_void_p(0x100000)
+    assert lib.lutc_correct_image_host(ctypes.byref(r), c, 1, out, 999, dws, ws, None) == E
+    assert lib.lutc_correct_image_host(ctypes.byref(r), c, 1, None, 1000, dws, ws, None) == E
+    assert lib.lutc_correct_image_host(ctypes.byref(r), c, 0, out, 1001, dws, wd, None) == E  # odd uint16 pitch
+    assert lib.lutc_correct_image_host(ctypes.byref(r), c, 1, out, 1000, dws, ws - 1, None) == _lib.LUTC_ENOMEM
+    assert lib.lutc_correct_image_host(ctypes.byref(r), c, 1, out, 1000, ctypes.c_void_p(0x100010), ws, None) == E
+    assert lib.lutc_correct_image_host(ctypes.byref(r), c, 2, out, 1000, dws, ws, None) == E
