@@ -234,7 +234,8 @@ enum {
     LUTC_TASK_APPLY = 5,         /**< in {raster, table}; out {out}; params width, height, bands, bits, table=u16|u8[, pitch, out_pitch] */
     LUTC_TASK_CORRECT_IMAGE = 6, /**< in {raster, A, G, O}; out {out}; params width, height, bands, bits[, stretch, pitch, out_pitch]; workspace */
     LUTC_TASK_DEVICE_INFO = 7,   /**< out {char buffer} (HOST); params capacity */
-    LUTC_TASK_DEMOSAIC = 8       /**< in {raster[, A, G, O]}; out {rgb}; params width, height, bits, pattern=rggb|bggr|grbg|gbrg[, pitch, out_pitch] */
+    LUTC_TASK_DEMOSAIC = 8,      /**< in {raster[, A, G, O]}; out {rgb}; params width, height, bits, pattern=rggb|bggr|grbg|gbrg[, pitch, out_pitch] */
+    LUTC_TASK_FIT = 9            /**< in {x, y}; out {coef, status[, q16]}; params width (detectors), height (lines), order, targets=line|sample[, pitch] */
 };
 
 #define LUTC_PARAMS_MAX 200 /**< longest parameter string (the paper's 200-byte header field) */
@@ -266,6 +267,41 @@ LUTC_API int lutc_submit(int task, const char* params, const void* const* inputs
  * document lists none.
  */
 LUTC_API int lutc_device_info(char* xml, size_t capacity, size_t* needed);
+
+/* ------------------------------------------------------------------------
+ * The paper's transport (Section II, Fig. 3): a TCP server in front of
+ * lutc_submit.
+ *
+ * Request: the 260-byte header -- task name (29 bytes, NUL-padded: "lutgen",
+ * "hist", "stretch", "compose", "apply", "correct_image", "device_info",
+ * "demosaic", "fit"), the byte '+', the parameter list (200 bytes,
+ * NUL-padded, as for lutc_submit) and the output name (30 bytes) -- then the
+ * payload length (uint64, little endian) and the payload: the task's inputs
+ * in lutc_submit's order, packed back to back, rasters and tables with packed
+ * rows (demosaic: the three coefficient arrays are optional).  Reply: status
+ * (int32, little endian), the output name echoed (30 bytes), the result
+ * length (uint64) and the task's outputs packed back to back (device_info:
+ * the XML text).  A malformed header, an unknown task or a payload whose
+ * length does not match the parameters is answered with LUTC_EINVAL and an
+ * empty result; the connection stays usable.
+ * ------------------------------------------------------------------------ */
+
+typedef struct lutc_net_server lutc_net_server;
+#define LUTC_NET_HEADER_BYTES 260
+
+/**
+ * Listens on `address` (dotted IPv4, NULL = 127.0.0.1) and `port` (0 = any
+ * free port, see lutc_net_server_port) and serves every connection on its own
+ * thread and CUDA stream of GPU `device`.  Returns LUTC_EINVAL for bad
+ * arguments, LUTC_EBUSY if the socket cannot be bound.
+ */
+LUTC_API int lutc_net_server_create(const char* address, int port, int device, lutc_net_server** out);
+/** The bound TCP port. */
+LUTC_API int lutc_net_server_port(const lutc_net_server* server);
+/** Requests answered so far, and how many of them with a non-zero status. */
+LUTC_API int lutc_net_server_stats(const lutc_net_server* server, uint64_t* requests, uint64_t* failures);
+/** Stops listening, closes every connection (after the request in progress) and frees the server. */
+LUTC_API int lutc_net_server_destroy(lutc_net_server* server);
 
 /* ------------------------------------------------------------------------
  * Bilinear Bayer demosaicing (Section III.A, case study 1), optionally fused

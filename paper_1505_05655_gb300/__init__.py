@@ -15,11 +15,13 @@ import ctypes
 import torch
 
 from ._lib import (LUTC_MAX_BANDS, LUTC_STRETCH, Coeffs, LutcError, Raster, check, lib)
+from . import net  # noqa: E402,F401  (the TCP transport's client side)
 
 __all__ = ["LutcError", "lib", "version", "lutgen", "apply_u16", "hist", "stretch", "compose", "apply_u8",
            "correct_image_workspace", "correct_image_tables", "correct_image", "apply_stretch", "trace_enable",
            "trace_read", "raster_desc", "coeff_descs", "set_tuning", "reset_tuning", "get_tuning", "Batch",
            "batch_autotune", "Server", "submit", "fit", "demosaic", "correct_image_host",
+           "net",
            "device_info"]
 
 

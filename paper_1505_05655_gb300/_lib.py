@@ -28,7 +28,7 @@ LUTC_PATH_TMA = 1
 LUTC_PATH_STRIP = 2
 LUTC_REQ_HOST = 2
 LUTC_TASK_LUTGEN, LUTC_TASK_HIST, LUTC_TASK_STRETCH, LUTC_TASK_COMPOSE = 1, 2, 3, 4
-LUTC_TASK_APPLY, LUTC_TASK_CORRECT_IMAGE, LUTC_TASK_DEVICE_INFO, LUTC_TASK_DEMOSAIC = 5, 6, 7, 8
+LUTC_TASK_APPLY, LUTC_TASK_CORRECT_IMAGE, LUTC_TASK_DEVICE_INFO, LUTC_TASK_DEMOSAIC, LUTC_TASK_FIT = 5, 6, 7, 8, 9
 LUTC_BAYER = {"rggb": 0, "bggr": 1, "grbg": 2, "gbrg": 3}
 
 
@@ -103,6 +103,10 @@ SIGNATURES = {
     "lutc_fit": (_I, [_P, _I64, _P, _I64, _I, _I, _I, _P, _P, _P, _P]),
     "lutc_correct_image_host_workspace": (_SZ, [ctypes.POINTER(Raster), _I]),
     "lutc_correct_image_host": (_I, [ctypes.POINTER(Raster), ctypes.POINTER(Coeffs), _I, _P, _I64, _P, _SZ, _P]),
+    "lutc_net_server_create": (_I, [ctypes.c_char_p, _I, _I, ctypes.POINTER(_P)]),
+    "lutc_net_server_port": (_I, [_P]),
+    "lutc_net_server_stats": (_I, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+    "lutc_net_server_destroy": (_I, [_P]),
     "lutc_demosaic": (_I, [ctypes.POINTER(Raster), ctypes.POINTER(Coeffs), _I, _P, _I64, _P]),
     "lutc_batch_workspace": (_SZ, [ctypes.POINTER(Job), _I]),
     "lutc_server_create": (_I, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]),

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "lutc.h"
 
 namespace lutc {
@@ -123,5 +125,19 @@ int sm_count();
 lutc_tuning tuning_for(int bits);  // the stored configuration (zeros = automatic)
 cudaEvent_t* trace_slot();         // LUTC_TRACE_PHASES + 1 events of the next traced call, or nullptr
 int cuda_status(cudaError_t e);  // cudaSuccess -> LUTC_OK, else LUTC_ECUDA (and clears the sticky-free error)
+
+// The task interface's parameter list (lutc_submit.cu): "key=value,..." of at most
+// LUTC_PARAMS_MAX bytes; -1 marks a key that was not given.
+struct TaskParams {
+    int64_t width = -1, height = -1, bands = 1, bits = -1, pitch = -1, out_pitch = -1, stretch = 1, capacity = -1;
+    int64_t order = -1;
+    int table = 0;    // 0 unset, 1 u16, 2 u8
+    int pattern = -1; // LUTC_BAYER_*
+    int targets = 0;  // fit: 0 one target per line, 1 one per sample
+};
+int parse_task_params(const char* text, TaskParams& p);
+bool task_params_ok(const TaskParams& p, bool width, bool height, bool bits);
+lutc_raster raster_of(const TaskParams& p, const void* data);
+std::vector<lutc_coeffs> coeffs_of(const TaskParams& p, const void* A, const void* G, const void* O);
 
 }  // namespace lutc

@@ -17,16 +17,10 @@
 
 #include "lutc_internal.cuh"
 
-namespace {
-
-struct Params {
-    int64_t width = -1, height = -1, bands = 1, bits = -1, pitch = -1, out_pitch = -1, stretch = 1, capacity = -1;
-    int table = 0;  // 0 unset, 1 u16, 2 u8
-    int pattern = -1;
-};
+namespace lutc {
 
 // "key=value,key=value": every key known, every value a non-negative decimal (or u16/u8 for table)
-int parse(const char* text, Params& p)
+int parse_task_params(const char* text, TaskParams& p)
 {
     if (!text) return LUTC_EINVAL;
     const size_t len = strnlen(text, LUTC_PARAMS_MAX + 1);
@@ -41,6 +35,12 @@ int parse(const char* text, Params& p)
         const size_t eq = item.find('=');
         if (eq == std::string::npos || eq == 0 || eq + 1 >= item.size()) return LUTC_EINVAL;
         const std::string key = item.substr(0, eq), val = item.substr(eq + 1);
+        if (key == "targets") {
+            if (val == "line") p.targets = 0;
+            else if (val == "sample") p.targets = 1;
+            else return LUTC_EINVAL;
+            continue;
+        }
         if (key == "pattern") {
             static const char* kNames[4] = {"rggb", "bggr", "grbg", "gbrg"};
             p.pattern = -1;
@@ -69,12 +69,13 @@ int parse(const char* text, Params& p)
         else if (key == "out_pitch") p.out_pitch = v;
         else if (key == "stretch") p.stretch = v;
         else if (key == "capacity") p.capacity = v;
+        else if (key == "order") p.order = v;
         else return LUTC_EINVAL;
     }
     return LUTC_OK;
 }
 
-bool need(const Params& p, bool width, bool height, bool bits)
+bool task_params_ok(const TaskParams& p, bool width, bool height, bool bits)
 {
     if (width && (p.width < 0 || p.width > INT32_MAX)) return false;
     if (height && (p.height < 0 || p.height > INT32_MAX)) return false;
@@ -82,7 +83,7 @@ bool need(const Params& p, bool width, bool height, bool bits)
     return p.bands >= 1 && p.bands <= LUTC_MAX_BANDS && (p.stretch == 0 || p.stretch == 1);
 }
 
-lutc_raster raster_of(const Params& p, const void* data)
+lutc_raster raster_of(const TaskParams& p, const void* data)
 {
     lutc_raster r;
     r.data = reinterpret_cast<const uint16_t*>(data);
@@ -95,7 +96,7 @@ lutc_raster raster_of(const Params& p, const void* data)
 }
 
 // per-band coefficient sets of [bands][width] arrays
-std::vector<lutc_coeffs> coeffs_of(const Params& p, const void* A, const void* G, const void* O)
+std::vector<lutc_coeffs> coeffs_of(const TaskParams& p, const void* A, const void* G, const void* O)
 {
     std::vector<lutc_coeffs> c(p.bands);
     for (int64_t b = 0; b < p.bands; ++b) {
@@ -107,45 +108,50 @@ std::vector<lutc_coeffs> coeffs_of(const Params& p, const void* A, const void* G
     return c;
 }
 
+namespace {
+
 int attr(cudaDeviceAttr a, int dev, int* v)
 {
     return cudaDeviceGetAttribute(v, a, dev) == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace
+}  // namespace lutc
+
+using namespace lutc;
 
 extern "C" int lutc_submit(int task, const char* params, const void* const* in, int n_in, void* const* out,
                            int n_out, void* workspace, size_t workspace_bytes, lutc_stream stream)
 {
-    Params p;
-    int rc = parse(params, p);
+    TaskParams p;
+    int rc = parse_task_params(params, p);
     if (rc) return rc;
     if (n_in < 0 || n_out < 0 || (n_in > 0 && !in) || (n_out > 0 && !out)) return LUTC_EINVAL;
     switch (task) {
     case LUTC_TASK_LUTGEN: {
-        if (!need(p, true, false, true) || n_in < 3 || n_out < 1) return LUTC_EINVAL;
+        if (!task_params_ok(p, true, false, true) || n_in < 3 || n_out < 1) return LUTC_EINVAL;
         lutc_coeffs c = {reinterpret_cast<const int32_t*>(in[0]), reinterpret_cast<const int32_t*>(in[1]),
                          reinterpret_cast<const int32_t*>(in[2]), (int32_t)p.width};
         return lutc_lutgen(&c, (int)p.bits, reinterpret_cast<uint16_t*>(out[0]), stream);
     }
     case LUTC_TASK_HIST: {
-        if (!need(p, true, true, true) || n_in < 4 || n_out < 1) return LUTC_EINVAL;
+        if (!task_params_ok(p, true, true, true) || n_in < 4 || n_out < 1) return LUTC_EINVAL;
         const lutc_raster r = raster_of(p, in[0]);
         const std::vector<lutc_coeffs> c = coeffs_of(p, in[1], in[2], in[3]);
         return lutc_hist(&r, c.data(), reinterpret_cast<uint64_t*>(out[0]), stream);
     }
     case LUTC_TASK_STRETCH: {
-        if (!need(p, false, false, true) || n_in < 1 || n_out < 2) return LUTC_EINVAL;
+        if (!task_params_ok(p, false, false, true) || n_in < 1 || n_out < 2) return LUTC_EINVAL;
         return lutc_stretch(reinterpret_cast<const uint64_t*>(in[0]), (int)p.bands, (int)p.bits,
                             reinterpret_cast<uint8_t*>(out[0]), reinterpret_cast<int32_t*>(out[1]), stream);
     }
     case LUTC_TASK_COMPOSE: {
-        if (!need(p, true, false, true) || n_in < 2 || n_out < 1) return LUTC_EINVAL;
+        if (!task_params_ok(p, true, false, true) || n_in < 2 || n_out < 1) return LUTC_EINVAL;
         return lutc_compose(reinterpret_cast<const uint16_t*>(in[0]), reinterpret_cast<const uint8_t*>(in[1]),
                             (int)p.width, (int)p.bits, reinterpret_cast<uint8_t*>(out[0]), stream);
     }
     case LUTC_TASK_APPLY: {
-        if (!need(p, true, true, true) || p.table == 0 || n_in < 2 || n_out < 1) return LUTC_EINVAL;
+        if (!task_params_ok(p, true, true, true) || p.table == 0 || n_in < 2 || n_out < 1) return LUTC_EINVAL;
         const lutc_raster r = raster_of(p, in[0]);
         if (p.table == 1)
             return lutc_apply_u16(&r, reinterpret_cast<const uint16_t*>(in[1]), reinterpret_cast<uint16_t*>(out[0]),
@@ -154,7 +160,7 @@ extern "C" int lutc_submit(int task, const char* params, const void* const* in, 
                              p.out_pitch >= 0 ? p.out_pitch : p.width, stream);
     }
     case LUTC_TASK_CORRECT_IMAGE: {
-        if (!need(p, true, true, true) || n_in < 4 || n_out < 1) return LUTC_EINVAL;
+        if (!task_params_ok(p, true, true, true) || n_in < 4 || n_out < 1) return LUTC_EINVAL;
         const lutc_raster r = raster_of(p, in[0]);
         const std::vector<lutc_coeffs> c = coeffs_of(p, in[1], in[2], in[3]);
         const int64_t elem = p.stretch ? 1 : 2;
@@ -163,7 +169,7 @@ extern "C" int lutc_submit(int task, const char* params, const void* const* in, 
                                   stream);
     }
     case LUTC_TASK_DEMOSAIC: {
-        if (!need(p, true, true, true) || p.bands != 1 || p.pattern < 0 || n_in < 1 || n_out < 1) return LUTC_EINVAL;
+        if (!task_params_ok(p, true, true, true) || p.bands != 1 || p.pattern < 0 || n_in < 1 || n_out < 1) return LUTC_EINVAL;
         const lutc_raster r = raster_of(p, in[0]);
         const bool correct = n_in >= 4;
         const lutc_coeffs c = correct ? lutc_coeffs{reinterpret_cast<const int32_t*>(in[1]),
@@ -172,6 +178,16 @@ extern "C" int lutc_submit(int task, const char* params, const void* const* in, 
                                       : lutc_coeffs{nullptr, nullptr, nullptr, 0};
         return lutc_demosaic(&r, correct ? &c : nullptr, p.pattern, reinterpret_cast<uint16_t*>(out[0]),
                              p.out_pitch >= 0 ? p.out_pitch : 2 * p.width, stream);
+    }
+    case LUTC_TASK_FIT: {
+        // width = detectors, height = calibration lines
+        if (p.width < 0 || p.width > INT32_MAX || p.height < 0 || p.height > INT32_MAX || n_in < 2 || n_out < 2)
+            return LUTC_EINVAL;
+        const int64_t xp = p.pitch >= 0 ? p.pitch : 2 * p.width;
+        return lutc_fit(reinterpret_cast<const uint16_t*>(in[0]), xp, reinterpret_cast<const double*>(in[1]),
+                        p.targets ? 8 * p.width : 0, (int)p.height, (int)p.width, (int)p.order,
+                        reinterpret_cast<double*>(out[0]), reinterpret_cast<int32_t*>(out[1]),
+                        n_out >= 3 ? reinterpret_cast<int32_t*>(out[2]) : nullptr, stream);
     }
     case LUTC_TASK_DEVICE_INFO: {
         if (p.capacity < 1 || n_out < 1) return LUTC_EINVAL;
