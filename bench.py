@@ -146,6 +146,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of per-rank timings over the process group (the slowest rank sets the time)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(pixels_per_rank: int, world: int, steps: int, ms: float) -> float:
+    """Gpixel/s of the whole job: every rank's pixels over the slowest rank's time."""
+    return pixels_per_rank * world * steps / (ms * 1e-3) / 1e9
+
+
 def workload_config(wl) -> dict:
     what = "full pipeline: detector LUT, 2/98 % stretch, uint8 out" if wl.stretch else "detector LUT only, uint16 out"
     in_bytes = wl.pixels * 2
@@ -291,12 +307,9 @@ def run_lutc(args, wl):
         timed(lambda: check(call()), k)
         phases = lutc.trace_read(k)
         lutc.trace_enable(0)
-    if ws > 1:
-        t = torch.tensor([ms, direct_ms], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, direct_ms = float(t[0].item()), float(t[1].item())
+    ms, direct_ms = max_over_ranks([ms, direct_ms], device)
     ms_step = ms / args.steps
-    value = wl.pixels * ws * args.steps / (ms * 1e-3) / 1e9
+    value = whole_job_rate(wl.pixels, ws, args.steps, ms)
 
     # keep this step's output for the parity check against the oracle below
     out_h.copy_(out)
@@ -369,10 +382,7 @@ def run_lutc(args, wl):
     e1.record(stream)
     barrier()
     sms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ems, sms], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ems, sms = float(t[0].item()), float(t[1].item())
+    ems, sms = max_over_ranks([ems, sms], device)
     line["e2e"] = {"value": wl.pixels * ws * e2e_steps / (ems * 1e-3) / 1e9, "unit": UNIT,
                    "h2d_bytes_per_step": raw_h.numel() * raw_h.element_size(),
                    "d2h_bytes_per_step": out_h.numel() * out_h.element_size(), "steps": e2e_steps,
@@ -721,6 +731,11 @@ def run_serve(args):
         print(json.dumps(line), flush=True)
 
 
+def _selected(args, name: str) -> bool:
+    words = [w for w in getattr(args, "cases", "").split(",") if w]
+    return not words or any(w in name for w in words)
+
+
 def fp64_peak_tflops(device) -> tuple[float, str]:
     """fp64 FMA-pipe peak: SMs x 2 fp64 FMA per clock x 2 flops x maximum SM clock."""
     import torch
@@ -760,6 +775,8 @@ def run_fit(args):
     shapes = {"paper": (6, 6000, 12), "large": (1024, 65536, 14)}
     res = {}
     for name, (n, ncols, bits) in shapes.items():
+        if not _selected(args, name):
+            continue
         x, y = synth.calib(synth.CALIB_SEED + rank, n, ncols, bits, dead_frac=0.01)
         xd, yd = torch.from_numpy(x).to(device), torch.from_numpy(y).to(device)
         per = {}
@@ -843,6 +860,8 @@ def run_demosaic(args):
              ("large 16384x16384 12-bit, fused detector correction", 16384, 16384, 12, True)]
     res = {}
     for name, h, w, bits, correct in cases:
+        if not _selected(args, name):
+            continue
         img = synth.raster(synth.CALIB_SEED + 7 + rank, 1, h, w, bits)[0]
         raw = torch.from_numpy(img).to(device)
         kw = {}
@@ -897,6 +916,8 @@ def main():
     ap.add_argument("--batch-images", type=int, default=256, help="images in the batch workload")
     ap.add_argument("--no-tune", action="store_true", help="batch workload: automatic configuration, no autotuner")
     ap.add_argument("--quick", action="store_true", help="scene line only (no batch and serving summaries)")
+    ap.add_argument("--cases", default="", help="fit / demosaic workloads: run only the cases whose name contains "
+                                                  "one of these comma-separated words")
     args = ap.parse_args()
     if args.workload == "batch" and args.impl != "reference":
         run_batch(args)
