@@ -139,21 +139,18 @@ __device__ __forceinline__ void stage_tile(const DemosaicArgs& a, int x0, int y0
 // Bayer role of a pixel under RGGB at parity (py, px): 0 R site, 1 G in a red row, 2 G in a blue row, 3 B site
 __host__ __device__ constexpr int role(int py, int px) { return py == 0 ? (px == 0 ? 0 : 1) : (px == 0 ? 2 : 3); }
 
-template <int PY, int PX, bool kCorrect>
-__global__ void __launch_bounds__(Tile<kCorrect>::threads, Tile<kCorrect>::min_blocks) k_demosaic(DemosaicArgs a)
+// One thread's 2 x 8 patch of the tile at (x0, y0): reads 4 staged rows of 12 values (staged
+// column c holds frame column x0 - 8 + c, staged row r frame row y0 - 1 + r) and writes the patch's
+// rows to the three planes.
+template <int PY, int PX, int kTW, int kTH, int kSW>
+__device__ __forceinline__ void patch(const uint16_t (*s)[kSW], int x0, int y0, int W, int H, uint8_t* out,
+                                      int64_t out_pitch, bool vout)
 {
-    using T = Tile<kCorrect>;
-    constexpr int kTW = T::W, kTH = T::H;
-    __shared__ __align__(16) uint16_t s[T::SH][T::SW];
-    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
-    stage_tile<kCorrect>(a, x0, y0, s);
-    __syncthreads();
-
     const int cx = threadIdx.x % (kTW / 8), ry = threadIdx.x / (kTW / 8);
     const int c0 = 8 + cx * 8;   // staged column of the patch's first pixel
     const int r0 = 1 + ry * 2;   // staged row of the patch's first row
     const int gx = x0 + cx * 8, gy = y0 + ry * 2;
-    if (gx >= a.W || gy >= a.H) return;
+    if (gx >= W || gy >= H) return;
 
     // 4 staged rows x 12 values (columns c0-2 .. c0+9)
     uint32_t v[4][12];
@@ -170,18 +167,18 @@ __global__ void __launch_bounds__(Tile<kCorrect>::threads, Tile<kCorrect>::min_b
     }
 
     // the block's halo is inside the image: every neighbour exists
-    const bool interior = x0 > 0 && y0 > 0 && x0 + kTW < a.W && y0 + kTH < a.H;
-    const bool full = a.vout && gx + 8 <= a.W;
+    const bool interior = x0 > 0 && y0 > 0 && x0 + kTW < W && y0 + kTH < H;
+    const bool full = vout && gx + 8 <= W;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
         const int y = gy + i;
-        if (y >= a.H) break;
-        const uint32_t nu = interior || y > 0, nd = interior || y + 1 < a.H;
-        uint32_t out[3][8];
+        if (y >= H) break;
+        const uint32_t nu = interior || y > 0, nd = interior || y + 1 < H;
+        uint32_t o[3][8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int x = gx + j;
-            const uint32_t nl = interior || x > 0, nr = interior || x + 1 < a.W;
+            const uint32_t nl = interior || x > 0, nr = interior || x + 1 < W;
             const uint32_t c = v[i + 1][j + 2];
             const uint32_t hs = v[i + 1][j + 1] + v[i + 1][j + 3];
             const uint32_t vs = v[i][j + 2] + v[i + 2][j + 2];
@@ -200,30 +197,41 @@ __global__ void __launch_bounds__(Tile<kCorrect>::threads, Tile<kCorrect>::min_b
                 vert = avg_n(vs, nv);
             }
             switch (role((i + PY) & 1, (j + PX) & 1)) {
-            case 0: out[0][j] = c; out[1][j] = orth; out[2][j] = diag; break;
-            case 1: out[0][j] = horiz; out[1][j] = c; out[2][j] = vert; break;
-            case 2: out[0][j] = vert; out[1][j] = c; out[2][j] = horiz; break;
-            default: out[0][j] = diag; out[1][j] = orth; out[2][j] = c; break;
+            case 0: o[0][j] = c; o[1][j] = orth; o[2][j] = diag; break;
+            case 1: o[0][j] = horiz; o[1][j] = c; o[2][j] = vert; break;
+            case 2: o[0][j] = vert; o[1][j] = c; o[2][j] = horiz; break;
+            default: o[0][j] = diag; o[1][j] = orth; o[2][j] = c; break;
             }
         }
         // this row of the patch in the three planes
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            uint16_t* row = reinterpret_cast<uint16_t*>(a.out + ((int64_t)k * a.H + y) * a.out_pitch);
+            uint16_t* row = reinterpret_cast<uint16_t*>(out + ((int64_t)k * H + y) * out_pitch);
             if (full) {
                 uint4 q;
-                q.x = out[k][0] | (out[k][1] << 16);
-                q.y = out[k][2] | (out[k][3] << 16);
-                q.z = out[k][4] | (out[k][5] << 16);
-                q.w = out[k][6] | (out[k][7] << 16);
+                q.x = o[k][0] | (o[k][1] << 16);
+                q.y = o[k][2] | (o[k][3] << 16);
+                q.z = o[k][4] | (o[k][5] << 16);
+                q.w = o[k][6] | (o[k][7] << 16);
                 *reinterpret_cast<uint4*>(row + gx) = q;
             } else {
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
-                    if (gx + j < a.W) row[gx + j] = (uint16_t)out[k][j];
+                    if (gx + j < W) row[gx + j] = (uint16_t)o[k][j];
             }
         }
     }
+}
+
+template <int PY, int PX, bool kCorrect>
+__global__ void __launch_bounds__(Tile<kCorrect>::threads, Tile<kCorrect>::min_blocks) k_demosaic(DemosaicArgs a)
+{
+    using T = Tile<kCorrect>;
+    __shared__ __align__(16) uint16_t s[T::SH][T::SW];
+    const int x0 = blockIdx.x * T::W, y0 = blockIdx.y * T::H;
+    stage_tile<kCorrect>(a, x0, y0, s);
+    __syncthreads();
+    patch<PY, PX, T::W, T::H, T::SW>(s, x0, y0, a.W, a.H, a.out, a.out_pitch, a.vout);
 }
 
 template <bool kCorrect>
@@ -268,8 +276,8 @@ extern "C" int lutc_demosaic(const lutc_raster* in, const lutc_coeffs* coeffs, i
     a.out_pitch = out_pitch_bytes;
     a.vin = ((uintptr_t)in->data % 16) == 0 && (in->pitch_bytes % 16) == 0;
     a.vout = ((uintptr_t)out % 16) == 0 && (out_pitch_bytes % 16) == 0;
-    if ((in->height + 15) / 16 > 65535) return LUTC_EUNSUPPORTED;  // grid rows of the raw path's 16-row tiles
     cudaStream_t st = (cudaStream_t)stream;
+    if ((in->height + 15) / 16 > 65535) return LUTC_EUNSUPPORTED;  // grid rows of the raw path's 16-row tiles
     if (coeffs)
         launch<true>(kPY[pattern], kPX[pattern], in->width, in->height, st, a);
     else

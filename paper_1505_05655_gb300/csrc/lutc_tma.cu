@@ -42,6 +42,7 @@
 #include <utility>
 
 #include "lutc_internal.cuh"
+#include "lutc_ptx.cuh"
 
 namespace lutc {
 
@@ -66,7 +67,6 @@ constexpr int kBarRegion = ((2 * kStages + 1) * 8 + 127) / 128 * 128;
 constexpr int kTableOffset = kRingBytes + kBarRegion;
 static_assert((2 * kStages + 1) * 8 <= kBarRegion, "barrier region");
 static_assert(kTableOffset % 128 == 0, "table alignment");
-constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
 
 enum Mode { kHist = kModeHist, kHistGlobal = kModeHistGlobal, kApplyStretch = kModeApplyStretch,
             kApplyDetector = kModeApplyDetector };
@@ -100,42 +100,21 @@ struct BatchArgs {
 };
 
 // ---------------------------------------------------------------------------
-// PTX wrappers: mbarrier, TMA
+// PTX wrappers: mbarrier, TMA (lutc_ptx.cuh); this file's waits record into g_device_status
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
-{
-    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
+using ptx::mbar_arrive;
+using ptx::mbar_arrive_expect_tx;
+using ptx::mbar_init;
+using ptx::mbar_try_wait;
+using ptx::smem_addr;
+using ptx::tma_load_2d;
+using ptx::tma_prefetch_map;
 
 // Wait for the phase of `bar` with the given parity; false after ~2 s (status recorded).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity);
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    return ptx::mbar_wait_bounded(bar, parity, &g_device_status);
+}
 
 // Barrier among the consumer threads only (the producer runs ahead), bounded like every wait.
 __device__ __forceinline__ bool consumer_sync(uint64_t* bar, uint32_t& phase)
@@ -144,34 +123,6 @@ __device__ __forceinline__ bool consumer_sync(uint64_t* bar, uint32_t& phase)
     const bool ok = mbar_wait(bar, phase);
     phase ^= 1u;
     return ok;
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > kWaitCycles) {
-            atomicCAS(&g_device_status, 0, LUTC_ETIMEOUT);
-            return false;
-        }
-    }
-    return true;
-}
-
-// Brings a tensor map held in global memory into the TMA unit's descriptor cache.
-__device__ __forceinline__ void tma_prefetch_map(const CUtensorMap* map)
-{
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-        "[%4];" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
-        : "memory");
 }
 
 // ---------------------------------------------------------------------------

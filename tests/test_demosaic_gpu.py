@@ -72,6 +72,23 @@ def test_fused_detector_correction(pattern, bits):
     np.testing.assert_array_equal(_gpu(img, w, pattern, bits, (A, G, O)), _ref(img, w, pattern, bits, (A, G, O)))
 
 
+# 16-byte aligned rows: the vector staging path, ragged in both directions, pitches padded to 16 bytes
+ALIGNED_SHAPES = [(67, 304, 0), (100, 1032, 0), (35, 144, 0), (34, 152, 0), (300, 1160, 0), (97, 300, 4), (259, 517, 3),
+              (1000, 2048, 0)]
+
+
+@pytest.mark.parametrize("pattern", PATTERNS)
+@pytest.mark.parametrize("h,w,pad", ALIGNED_SHAPES)
+def test_aligned_rows_raw_and_corrected(pattern, h, w, pad):
+    bits = 12
+    img = _raw(7 + h + w, h, w, bits, pad=pad)
+    assert (img.strides[0] % 16) == 0
+    A, G, O = synth.coeffs(7 + h, 0, w)
+    A[::29] = 900  # int64 columns
+    np.testing.assert_array_equal(_gpu(img, w, pattern, bits), _ref(img, w, pattern, bits))
+    np.testing.assert_array_equal(_gpu(img, w, pattern, bits, (A, G, O)), _ref(img, w, pattern, bits, (A, G, O)))
+
+
 @pytest.mark.parametrize("in_off,pad,out_pad", [(1, 3, 1), (3, 0, 5), (0, 8, 0), (5, 1, 3)])
 def test_unaligned_rows(in_off, pad, out_pad):
     h, w = 45, 263
