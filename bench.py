@@ -420,6 +420,11 @@ def run_lutc(args, wl):
                           "latency_ms": {r: {"p50": d["p50_ms"], "p99": d["p99_ms"], "gpx_s": d["gpx_s"],
                                              "mean_batch": d["mean_batch"]} for r, d in v["latency"].items()},
                           "outputs_equal_single_calls": v["outputs_equal_single_calls"],
+                          "host_requests": {"saturation_gpx_s": v["host_requests"]["saturation"]["gpx_s"],
+                                            "p50_ms_200": v["host_requests"]["latency_200"]["p50_ms"],
+                                            "p99_ms_200": v["host_requests"]["latency_200"]["p99_ms"],
+                                            "outputs_equal_single_calls":
+                                                v["host_requests"]["outputs_equal_single_calls"]},
                           "config": v["config"]["workload"]}
         line["fit"] = run_fit(sub)
         line["demosaic"] = run_demosaic(sub)
@@ -645,6 +650,7 @@ def run_serve(args):
     pool_per_sensor = 4
     server = lutc.Server(budget_bytes=40 << 30, max_batch=32, max_wait_us=2000, streams=3)
     pool = []  # (sensor, raster on device, output on device, pixels)
+    pool_host = []  # (sensor, raster in pinned host memory, output in pinned host memory, pixels, keep, keep)
     for sid in range(nsens):
         W, B, Bt = int(w[sid]), int(bands[sid]), int(bits[sid])
         A, G, O = synth.coeff_set(synth.batch_image_seed(synth.SERVE_SEED, sid), B, W)
@@ -660,10 +666,20 @@ def run_serve(args):
             opitch = -(-W // 16) * 16
             out = torch.empty((B, H, opitch), dtype=torch.uint8, device=device)[:, :, :W]
             pool.append((sid, raw, out, B * H * W))
+            if (sid * pool_per_sensor + k) % 16 == 0:
+                # every 16th raster also from pinned host memory (the server stages it in and out); a small
+                # set of reused host buffers, like a receiver's: a 10 GB page-locked working set slows
+                # every host access down (address translation), whichever engine copies
+                raw_h = torch.from_numpy(host).pin_memory()
+                out_h = torch.empty((B, H, opitch), dtype=torch.uint8).pin_memory()
+                pool_host.append((sid, raw_h[:, :, :W].numpy(), out_h[:, :, :W].numpy(), B * H * W, raw_h, out_h))
     rng = np.random.default_rng(synth.SERVE_SEED)
+    used_dev, used_host = set(), set()
 
-    def drive(rate, n, closed=False):
-        picks = rng.integers(0, len(pool), n)
+    def drive(rate, n, closed=False, host=False):
+        used = used_host if host else used_dev
+        src = pool_host if host else pool
+        picks = rng.integers(0, len(src), n)
         gaps = rng.exponential(1.0 / rate, n) if rate else np.zeros(n)
         sched = np.cumsum(gaps)
         tickets = [None] * n
@@ -676,9 +692,9 @@ def run_serve(args):
                     dt = t0 + sched[i] - time.monotonic()
                     if dt > 0:
                         time.sleep(dt)
-                sid, raw, out, _ = pool[picks[i]]
+                sid, raw, out = src[picks[i]][:3]
                 while True:
-                    rc, t = server.try_submit(sid, raw, out)
+                    rc, t = server.try_submit(sid, raw, out, host=host)
                     if rc == 0:
                         break
                     time.sleep(0.0002)  # queue full under a closed-loop burst
@@ -692,9 +708,10 @@ def run_serve(args):
             infos[i] = server.wait(tickets[i])
         th.join()
         lat = np.array([infos[i].done_s - (t0 + sched[i] if not closed else infos[i].submit_s) for i in range(n)])
-        px = sum(pool[j][3] for j in picks)
+        px = sum(src[j][3] for j in picks)
         span = max(i.done_s for i in infos) - min(i.submit_s for i in infos)
         bad = sum(1 for i in infos if i.status != 0)
+        used.update(int(j) for j in picks)
         prep = np.array([i.launched_s - i.start_s for i in infos])
         run = np.array([i.done_s - i.launched_s for i in infos])
         return dict(p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
@@ -707,9 +724,21 @@ def run_serve(args):
     for rate, n in ((50, max(200, args.steps // 4)), (200, max(400, args.steps)), (800, max(400, 2 * args.steps))):
         loads[str(rate)] = drive(rate, n)
     sat = drive(0, max(500, 2 * args.steps), closed=True)
+    # requests from pinned host memory: staged in and out by the server (copies inside each request's latency)
+    host_sat = drive(0, max(300, args.steps), closed=True, host=True)
+    host_200 = drive(200, max(300, args.steps // 2), host=True)
+    host_exact = True
+    for k in sorted(used_host)[::9]:  # entries some request wrote
+        sid, raw_np, out_np = pool_host[k][:3]
+        b = raw_np.shape[0]
+        A, G, O = synth.coeff_set(synth.batch_image_seed(synth.SERVE_SEED, sid), b, raw_np.shape[2])
+        d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        ref = lutc.correct_image(d(raw_np), d(A), d(G), d(O), int(bits[sid])).cpu().numpy()
+        host_exact = host_exact and bool(np.array_equal(ref, out_np))
     # each pool raster's output must equal a single call on it
     exact = True
-    for sid, raw, out, _ in pool[::9]:
+    for k in sorted(used_dev)[::9]:
+        sid, raw, out, _ = pool[k]
         b = raw.shape[0]
         A, G, O = synth.coeff_set(synth.batch_image_seed(synth.SERVE_SEED, sid), b, raw.shape[2])
         d = lambda a: torch.from_numpy(a).to(device)
@@ -724,7 +753,10 @@ def run_serve(args):
                                    "2 ms, 3 streams" % (nsens, pool_per_sensor),
                        "l2": "inputs larger than L2 (pool %.1f GB)" % (sum(p_[3] for p_ in pool) * 2 / 1e9)},
             "latency": loads, "saturation": sat, "warmup_with_cache_misses": warm, "server": st,
-            "outputs_equal_single_calls": exact}
+            "outputs_equal_single_calls": exact,
+            "host_requests": {"saturation": host_sat, "latency_200": host_200, "outputs_equal_single_calls": host_exact,
+                              "path": "LUTC_REQ_HOST: rasters and outputs in pinned host memory (16 reused buffers), staged by "
+                                      "the server with SM-driven row copies"}}
     if getattr(args, "_return", False):
         return line
     if rank == 0:
@@ -732,7 +764,7 @@ def run_serve(args):
 
 
 def _selected(args, name: str) -> bool:
-    words = [w for w in getattr(args, "cases", "").split(",") if w]
+    words = [w.replace("_", " ") for w in getattr(args, "cases", "").split(",") if w]
     return not words or any(w in name for w in words)
 
 
@@ -917,7 +949,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="batch workload: automatic configuration, no autotuner")
     ap.add_argument("--quick", action="store_true", help="scene line only (no batch and serving summaries)")
     ap.add_argument("--cases", default="", help="fit / demosaic workloads: run only the cases whose name contains "
-                                                  "one of these comma-separated words")
+                                                  "one of these comma-separated words ('_' stands for a space)")
     args = ap.parse_args()
     if args.workload == "batch" and args.impl != "reference":
         run_batch(args)

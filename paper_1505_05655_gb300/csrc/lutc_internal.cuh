@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "lutc.h"
@@ -116,6 +117,12 @@ int pass1_accumulate(const lutc_raster* in, const lutc_coeffs* per_band, unsigne
 int pass2(const lutc_raster* in, const lutc_coeffs* per_band, const uint8_t* S, void* out, int64_t out_pitch,
           bool stretch, cudaStream_t st);
 size_t tables_bytes(const lutc_raster* in);
+
+// Row copies by the SMs (lutc_copy.cu): `rows` rows of `width` bytes from src (pitch spitch) to dst
+// (pitch dpitch), any mix of device memory and device-accessible (page-locked) host memory.
+int copy_rows(void* dst, int64_t dpitch, const void* src, int64_t spitch, int64_t width, int64_t rows,
+              cudaStream_t st);
+bool device_can_access(const void* p);  // page-locked host, device or managed memory at the same address
 void tables_offsets(const lutc_raster* in, size_t* hist, size_t* S, size_t* lohi);
 
 // returns LUTC_OK or LUTC_EINVAL

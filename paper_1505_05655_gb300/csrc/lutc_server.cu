@@ -116,6 +116,7 @@ struct Request {
     bool done = false;
     size_t in_off = 0, in_bytes = 0, out_off = 0, out_bytes = 0;  // staging (host requests)
     int64_t dpitch = 0, dopitch = 0;
+    bool sm_copy = false;  // host buffers the kernels can address: rows copied by the SMs
 };
 
 struct Flight {
@@ -283,27 +284,35 @@ int lutc_server_st::launch(Flight* f)
         return LUTC_OK;
     }
     int rc;
-    for (int i = 0; i < n; ++i) {
-        Request* r = f->reqs[i];
-        if (!(r->flags & LUTC_REQ_HOST)) continue;
-        const Sensor& s = *f->sensors[i];
-        if ((rc = cuda_status(cudaMemcpy2DAsync(dev(r->in_off), r->dpitch, r->in, r->pitch, 2 * (size_t)s.width,
-                                                (size_t)s.bands * r->H, cudaMemcpyHostToDevice, st))))
-            return rc;
-    }
+    // The plan first: its tables go to the device from host memory, a copy that waits for the
+    // stream's earlier work, so it must not queue behind this batch's own copies in.
     const size_t need = lutc_batch_workspace(jobs.data(), n);
     if (need > f->ws_bytes) return LUTC_ENOMEM;
     const lutc_batch_config bc = {0, 0, 0};
     if ((rc = lutc_batch_create(jobs.data(), n, &bc, dev(f->ws_off), f->ws_bytes, (lutc_stream)st, &f->batch)))
         return rc;
+    for (int i = 0; i < n; ++i) {
+        Request* r = f->reqs[i];
+        if (!(r->flags & LUTC_REQ_HOST)) continue;
+        const Sensor& s = *f->sensors[i];
+        rc = r->sm_copy ? copy_rows(dev(r->in_off), r->dpitch, r->in, r->pitch, 2 * (int64_t)s.width,
+                                    (int64_t)s.bands * r->H, st)
+                        : cuda_status(cudaMemcpy2DAsync(dev(r->in_off), r->dpitch, r->in, r->pitch,
+                                                        2 * (size_t)s.width, (size_t)s.bands * r->H,
+                                                        cudaMemcpyHostToDevice, st));
+        if (rc) return rc;
+    }
     if ((rc = lutc_batch_run(f->batch, (lutc_stream)st))) return rc;
     for (int i = 0; i < n; ++i) {
         Request* r = f->reqs[i];
         if (!(r->flags & LUTC_REQ_HOST)) continue;
         const Sensor& s = *f->sensors[i];
-        if ((rc = cuda_status(cudaMemcpy2DAsync(r->out, r->out_pitch, dev(r->out_off), r->dopitch, (size_t)s.width,
-                                                (size_t)s.bands * r->H, cudaMemcpyDeviceToHost, st))))
-            return rc;
+        rc = r->sm_copy ? copy_rows(r->out, r->out_pitch, dev(r->out_off), r->dopitch, (int64_t)s.width,
+                                    (int64_t)s.bands * r->H, st)
+                        : cuda_status(cudaMemcpy2DAsync(r->out, r->out_pitch, dev(r->out_off), r->dopitch,
+                                                        (size_t)s.width, (size_t)s.bands * r->H,
+                                                        cudaMemcpyDeviceToHost, st));
+        if (rc) return rc;
     }
     return cuda_status(cudaEventRecord(events[f->slot], st));
 }
@@ -551,6 +560,10 @@ extern "C" int lutc_server_submit(lutc_server s, int sensor_id, const uint16_t* 
                                   uint64_t* ticket)
 {
     if (!s || !ticket || height < 1 || (flags & ~LUTC_REQ_HOST)) return LUTC_EINVAL;
+    // host buffers the kernels can address (page-locked memory) are copied by the SMs: a request's
+    // short strided rows are slow for the copy engines
+    const bool sm_copy = (flags & LUTC_REQ_HOST) && !s->cfg.fake_device && raster && out &&
+                         device_can_access(raster) && device_can_access(out);
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) return LUTC_ESHUTDOWN;
     auto it = s->sensors.find(sensor_id);
@@ -573,6 +586,7 @@ extern "C" int lutc_server_submit(lutc_server s, int sensor_id, const uint16_t* 
     r->pitch = pitch_bytes;
     r->out = out;
     r->out_pitch = out_pitch_bytes;
+    r->sm_copy = sm_copy;
     r->t_submit = now_s();
     s->tickets[r->ticket] = r;
     s->pending.push_back(r);
