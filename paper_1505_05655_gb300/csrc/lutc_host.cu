@@ -135,6 +135,24 @@ extern "C" int lutc_correct_image_host(const lutc_raster* in, const lutc_coeffs*
     if (good && stretch) good = ok(cudaMemsetAsync(hist, 0, (size_t)bands * L * 8, st));
     const uint8_t* hin = reinterpret_cast<const uint8_t*>(in->data);
     uint8_t* hout = reinterpret_cast<uint8_t*>(out);
+    // Rows packed on both sides: one linear copy per chunk.  Strided rows: the SMs copy them when the
+    // host buffer is device-addressable (the copy engines move short strided rows slowly), else a 2-D copy.
+    // (packed: no gap between rows on either side, so a linear copy touches exactly the rows' bytes)
+    const bool in_packed = in->pitch_bytes == 2 * (int64_t)W && l.raw_pitch == 2 * (int64_t)W;
+    const bool out_packed = out_pitch_bytes == elem * W && l.out_pitch == elem * W;
+    const bool in_sm = !in_packed && device_can_access(in->data), out_sm = !out_packed && device_can_access(out);
+    auto copy_in = [&](void* dst, const uint8_t* src, int64_t nr) {
+        if (in_packed) return ok(cudaMemcpyAsync(dst, src, (size_t)nr * l.raw_pitch, cudaMemcpyDefault, p->h2d));
+        if (in_sm) return copy_rows(dst, l.raw_pitch, src, in->pitch_bytes, 2 * (int64_t)W, nr, p->h2d) == LUTC_OK;
+        return ok(cudaMemcpy2DAsync(dst, l.raw_pitch, src, in->pitch_bytes, 2 * (size_t)W, (size_t)nr,
+                                    cudaMemcpyDefault, p->h2d));
+    };
+    auto copy_out = [&](uint8_t* dst, const uint8_t* src, int64_t nr) {
+        if (out_packed) return ok(cudaMemcpyAsync(dst, src, (size_t)nr * l.out_pitch, cudaMemcpyDefault, p->d2h));
+        if (out_sm) return copy_rows(dst, out_pitch_bytes, src, l.out_pitch, elem * (int64_t)W, nr, p->d2h) == LUTC_OK;
+        return ok(cudaMemcpy2DAsync(dst, out_pitch_bytes, src, l.out_pitch, elem * (size_t)W, (size_t)nr,
+                                    cudaMemcpyDefault, p->d2h));
+    };
     for (int b = 0; good && b < bands; ++b) {
         lutc_raster band = dev_all;
         band.bands = 1;
@@ -151,9 +169,7 @@ extern "C" int lutc_correct_image_host(const lutc_raster* in, const lutc_coeffs*
             int64_t r0, nr;
             chunk(c, &r, &r0, &nr);
             cudaEvent_t in_done = ev();
-            good = ok(cudaMemcpy2DAsync(const_cast<uint16_t*>(r.data), l.raw_pitch,
-                                        hin + ((int64_t)b * H + r0) * in->pitch_bytes, in->pitch_bytes,
-                                        2 * (size_t)W, (size_t)nr, cudaMemcpyDefault, p->h2d)) &&
+            good = copy_in(const_cast<uint16_t*>(r.data), hin + ((int64_t)b * H + r0) * in->pitch_bytes, nr) &&
                    ok(cudaEventRecord(in_done, p->h2d)) && ok(cudaStreamWaitEvent(st, in_done, 0));
             if (good && stretch) good = pass1_accumulate(&r, cb, hist + b * L, st) == LUTC_OK;
         }
@@ -166,8 +182,7 @@ extern "C" int lutc_correct_image_host(const lutc_raster* in, const lutc_coeffs*
             cudaEvent_t out_ready = ev();
             good = pass2(&r, cb, stretch ? S + b * L : nullptr, o, l.out_pitch, stretch, st) == LUTC_OK &&
                    ok(cudaEventRecord(out_ready, st)) && ok(cudaStreamWaitEvent(p->d2h, out_ready, 0)) &&
-                   ok(cudaMemcpy2DAsync(hout + ((int64_t)b * H + r0) * out_pitch_bytes, out_pitch_bytes, o,
-                                        l.out_pitch, elem * (size_t)W, (size_t)nr, cudaMemcpyDefault, p->d2h));
+                   copy_out(hout + ((int64_t)b * H + r0) * out_pitch_bytes, o, nr);
         }
     }
     // the caller's stream continues after the last copy out (also after a failure part way)
