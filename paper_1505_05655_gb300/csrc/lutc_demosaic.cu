@@ -9,7 +9,8 @@
 // neighbours; at a green site, one colour from the left/right pair and the
 // other from the up/down pair.
 //
-// GB300 mapping: a block owns a 128-column tile (16 rows raw, 32 rows with
+// GB300 mapping: frames with 16-byte aligned rows take the TMA-fed persistent
+// kernel below; the others a block per tile (16 rows raw, 32 rows with
 // correction; see Tile).  The tile and a halo (one row above and below, one
 // 8-column chunk left and right, so every load is an aligned vector) is staged
 // in shared memory, corrected on the way in when coefficients are given (the
@@ -23,7 +24,10 @@
 // pixel: 2 bytes in, 6 bytes out (the halo re-reads hit L2).
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "lutc_internal.cuh"
+#include "lutc_ptx.cuh"
 
 namespace lutc {
 namespace {
@@ -234,6 +238,155 @@ __global__ void __launch_bounds__(Tile<kCorrect>::threads, Tile<kCorrect>::min_b
     patch<PY, PX, T::W, T::H, T::SW>(s, x0, y0, a.W, a.H, a.out, a.out_pitch, a.vout);
 }
 
+// ---------------------------------------------------------------------------
+// TMA-fed persistent version (frames with 16-byte aligned rows, at least one
+// staged tile in each direction).  A block keeps two 128 x 32 tiles (with
+// their halo) in flight through cp.async.bulk.tensor loads into a 2-stage
+// ring (zeros outside the frame) while it computes the current one.  The
+// grid is one wave and the blocks sweep the frame together: at step k block
+// b takes tile k x gridDim + b in row-major tile order, so at any moment all
+// blocks work on the same few rows of tiles and share DRAM pages.  (A walk
+// where each block took its own contiguous run of tiles was slower than the
+// plain kernel, 580 against 474 us at 16384^2, and so was a grid of whole
+// blocks per column strip, which leaves SMs unevenly loaded: 465 us.)
+// With correction, the block corrects each staged tile in place before the
+// interpolation: a thread owns 4 staged columns (their coefficients read
+// per tile) and a seventh of the rows.
+// ---------------------------------------------------------------------------
+constexpr int kQW = 128, kQH = 32, kQSW = kQW + 16, kQSH = kQH + 2, kQThreads = (kQW / 8) * (kQH / 2);
+constexpr int kQStages = 2;
+constexpr int kQStageElems = (kQSW * kQSH + 63) / 64 * 64;  // stages 128-byte aligned
+constexpr uint32_t kQBoxBytes = kQSW * kQSH * 2;
+constexpr int kQLanes = kQThreads / (kQSW / 4);             // correction: row lanes of 36 x 4 columns
+static_assert(kQThreads == 256 && kQLanes >= 1, "tile geometry");
+
+struct DemosaicTmaArgs {
+    CUtensorMap map;   // uint16 [H][W], row stride = pitch, box {kQSW, kQSH}
+    int W, H, bits;
+    BandCoef coef;     // A == nullptr: no correction
+    uint8_t* out;
+    int64_t out_pitch;
+    int vout;
+    int strips;        // column strips of kQW columns (tiles per tile row)
+    int64_t ntiles;    // strips x tile rows
+    int* status;       // the library's kernel status word
+};
+
+template <int PY, int PX, bool kCorrect>
+__global__ void __launch_bounds__(kQThreads, 3) k_demosaic_tma(const __grid_constant__ DemosaicTmaArgs a)
+{
+    __shared__ __align__(128) uint16_t ring[kQStages][kQStageElems];
+    __shared__ __align__(8) uint64_t full[kQStages];
+    const int tid = threadIdx.x;
+    const int64_t n = (int64_t)blockIdx.x < a.ntiles ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    if (n == 0) return;  // the whole block, before any barrier exists
+    if (tid == 0) {
+        for (int s = 0; s < kQStages; ++s) ptx::mbar_init(&full[s], 1);
+        ptx::fence_mbar_init();
+    }
+    __syncthreads();
+    auto tile_of = [&](int64_t k, int* x0, int* y0) {
+        const int64_t t = k * gridDim.x + blockIdx.x;
+        const int64_t ty = t / a.strips;
+        *x0 = (int)(t - ty * a.strips) * kQW;
+        *y0 = (int)ty * kQH;
+    };
+    auto issue = [&](int64_t k) {  // thread 0: the block's k-th tile into stage k % kQStages
+        int x0, y0;
+        tile_of(k, &x0, &y0);
+        uint64_t* bar = &full[k % kQStages];
+        ptx::mbar_arrive_expect_tx(bar, kQBoxBytes);
+        ptx::tma_load_2d(ring[k % kQStages], &a.map, bar, x0 - 8, y0 - 1);
+    };
+    if (tid == 0)
+        for (int64_t k = 0; k < n && k < kQStages; ++k) issue(k);
+
+    const int32_t M = (1 << a.bits) - 1;
+    const int q = tid % (kQSW / 4), lane = tid / (kQSW / 4);
+    int64_t k = 0;
+    for (; k < n; ++k) {
+        const int s = (int)(k % kQStages);
+        int x0, y0;
+        tile_of(k, &x0, &y0);
+        const bool ok = ptx::mbar_wait_bounded(&full[s], (uint32_t)((k / kQStages) & 1), a.status);
+        if (!__syncthreads_and(ok)) break;  // the same decision in every thread
+        uint16_t (*st)[kQSW] = reinterpret_cast<uint16_t (*)[kQSW]>(ring[s]);
+        if (kCorrect) {
+            if (lane < kQLanes) {
+                int32_t cA[4], cG[4], cO[4];
+                bool fits[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int gx = x0 - 8 + q * 4 + j;
+                    const bool in = gx >= 0 && gx < a.W;
+                    cA[j] = in ? __ldg(a.coef.A + gx) : 0;
+                    cG[j] = in ? __ldg(a.coef.G + gx) : 0;
+                    cO[j] = in ? __ldg(a.coef.O + gx) : 0;
+                    fits[j] = col_fits_i32(cA[j], cG[j], cO[j], M);
+                    if (fits[j]) cO[j] += 32768;
+                }
+                for (int r = lane; r < kQSH; r += kQLanes) {
+                    const int gy = y0 - 1 + r;
+                    if (gy < 0 || gy >= a.H) continue;  // zeros from the load stay zeros
+                    uint2 w = *reinterpret_cast<const uint2*>(&st[r][q * 4]);
+                    uint32_t v[4] = {w.x & 0xffffu, w.x >> 16, w.y & 0xffffu, w.y >> 16};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int gx = x0 - 8 + q * 4 + j;
+                        if (gx >= 0 && gx < a.W) {
+                            const uint32_t x = min(v[j], (uint32_t)M);
+                            v[j] = fits[j] ? det_i32(cA[j], cG[j], cO[j], x, M) : det_i64(cA[j], cG[j], cO[j], x, M);
+                        }
+                    }
+                    w.x = v[0] | (v[1] << 16);
+                    w.y = v[2] | (v[3] << 16);
+                    *reinterpret_cast<uint2*>(&st[r][q * 4]) = w;
+                }
+            }
+            __syncthreads();
+        }
+        patch<PY, PX, kQW, kQH, kQSW>(st, x0, y0, a.W, a.H, a.out, a.out_pitch, a.vout != 0);
+        __syncthreads();  // every thread is done with stage s
+        if (tid == 0 && k + kQStages < n) {
+            ptx::fence_proxy_async_smem();  // this block's generic accesses to the stage come before the reload
+            issue(k + kQStages);
+        }
+    }
+    if (k < n && tid == 0) {
+        // a load did not arrive in time: wait (bounded) for the ones still in flight before leaving
+        for (int64_t j = k; j < n && j < k + kQStages; ++j)
+            ptx::mbar_wait_bounded(&full[j % kQStages], (uint32_t)((j / kQStages) & 1), a.status);
+    }
+}
+
+template <bool kCorrect>
+int launch_tma(int py, int px, cudaStream_t st, DemosaicTmaArgs& a)
+{
+    static int per_sm_cache[2][64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LUTC_ECUDA;
+    int& per_sm = per_sm_cache[kCorrect][dev];
+    if (per_sm == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_demosaic_tma<0, 0, kCorrect>, kQThreads, 0) !=
+                cudaSuccess ||
+            b < 1) {
+            cudaGetLastError();
+            b = 1;
+        }
+        per_sm = b;
+    }
+    // one wave, never more blocks than tiles
+    const int64_t blocks = std::min<int64_t>(a.ntiles, (int64_t)sm_count() * per_sm);
+    switch (2 * py + px) {
+    case 0: k_demosaic_tma<0, 0, kCorrect><<<(unsigned)blocks, kQThreads, 0, st>>>(a); break;
+    case 1: k_demosaic_tma<0, 1, kCorrect><<<(unsigned)blocks, kQThreads, 0, st>>>(a); break;
+    case 2: k_demosaic_tma<1, 0, kCorrect><<<(unsigned)blocks, kQThreads, 0, st>>>(a); break;
+    default: k_demosaic_tma<1, 1, kCorrect><<<(unsigned)blocks, kQThreads, 0, st>>>(a); break;
+    }
+    return cuda_status(cudaGetLastError());
+}
+
 template <bool kCorrect>
 void launch(int py, int px, int W, int H, cudaStream_t st, const DemosaicArgs& a)
 {
@@ -277,6 +430,32 @@ extern "C" int lutc_demosaic(const lutc_raster* in, const lutc_coeffs* coeffs, i
     a.vin = ((uintptr_t)in->data % 16) == 0 && (in->pitch_bytes % 16) == 0;
     a.vout = ((uintptr_t)out % 16) == 0 && (out_pitch_bytes % 16) == 0;
     cudaStream_t st = (cudaStream_t)stream;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    int* status = device_status_ptr();
+    if (enc && status && ((uintptr_t)in->data % 16) == 0 && (in->pitch_bytes % 16) == 0 && in->width >= kQSW &&
+        in->height >= kQSH) {
+        DemosaicTmaArgs t;
+        const cuuint64_t dims[2] = {(cuuint64_t)in->width, (cuuint64_t)in->height};
+        const cuuint64_t strides[1] = {(cuuint64_t)in->pitch_bytes};
+        const cuuint32_t box[2] = {(cuuint32_t)kQSW, (cuuint32_t)kQSH};
+        const cuuint32_t estr[2] = {1, 1};
+        if (enc(&t.map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<uint16_t*>(in->data), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+            t.W = in->width;
+            t.H = in->height;
+            t.bits = in->bits;
+            t.coef = a.coef;
+            t.out = a.out;
+            t.out_pitch = a.out_pitch;
+            t.vout = a.vout;
+            t.strips = (in->width + kQW - 1) / kQW;
+            t.ntiles = (int64_t)t.strips * ((in->height + kQH - 1) / kQH);
+            t.status = status;
+            return coeffs ? launch_tma<true>(kPY[pattern], kPX[pattern], st, t)
+                          : launch_tma<false>(kPY[pattern], kPX[pattern], st, t);
+        }
+    }
     if ((in->height + 15) / 16 > 65535) return LUTC_EUNSUPPORTED;  // grid rows of the raw path's 16-row tiles
     if (coeffs)
         launch<true>(kPY[pattern], kPX[pattern], in->width, in->height, st, a);

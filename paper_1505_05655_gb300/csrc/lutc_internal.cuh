@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -132,6 +133,8 @@ int sm_count();
 lutc_tuning tuning_for(int bits);  // the stored configuration (zeros = automatic)
 cudaEvent_t* trace_slot();         // LUTC_TRACE_PHASES + 1 events of the next traced call, or nullptr
 int cuda_status(cudaError_t e);  // cudaSuccess -> LUTC_OK, else LUTC_ECUDA (and clears the sticky-free error)
+int* device_status_ptr();        // the kernel status word (lutc_device_status) of the current device, or nullptr
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();  // cuTensorMapEncodeTiled, or nullptr
 
 // The task interface's parameter list (lutc_submit.cu): "key=value,..." of at most
 // LUTC_PARAMS_MAX bytes; -1 marks a key that was not given.

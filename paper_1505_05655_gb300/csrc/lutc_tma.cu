@@ -793,6 +793,29 @@ int tma_batch_pass(const BatchLaunch& b, int mode, int column_threads, int block
 
 }  // namespace lutc
 
+namespace lutc {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() { return encode_fn(); }
+
+// Device address of this library's kernel status word on the current device (for kernels of other files).
+int* device_status_ptr()
+{
+    static int* ptrs[64] = {};
+    static std::mutex mu;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptrs[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_device_status) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        ptrs[dev] = reinterpret_cast<int*>(p);
+    }
+    return ptrs[dev];
+}
+}  // namespace lutc
+
 extern "C" int lutc_device_status(int* status, lutc_stream stream)
 {
     if (!status) return LUTC_EINVAL;
