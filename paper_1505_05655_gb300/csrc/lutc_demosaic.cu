@@ -325,22 +325,37 @@ __global__ void __launch_bounds__(kQThreads, 3) k_demosaic_tma(const __grid_cons
                     fits[j] = col_fits_i32(cA[j], cG[j], cO[j], M);
                     if (fits[j]) cO[j] += 32768;
                 }
-                for (int r = lane; r < kQSH; r += kQLanes) {
-                    const int gy = y0 - 1 + r;
-                    if (gy < 0 || gy >= a.H) continue;  // zeros from the load stay zeros
-                    uint2 w = *reinterpret_cast<const uint2*>(&st[r][q * 4]);
-                    uint32_t v[4] = {w.x & 0xffffu, w.x >> 16, w.y & 0xffffu, w.y >> 16};
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int gx = x0 - 8 + q * 4 + j;
-                        if (gx >= 0 && gx < a.W) {
-                            const uint32_t x = min(v[j], (uint32_t)M);
-                            v[j] = fits[j] ? det_i32(cA[j], cG[j], cO[j], x, M) : det_i64(cA[j], cG[j], cO[j], x, M);
-                        }
+                // rows of the frame only (zeros from the load stay zeros)
+                const int r_lo = max(lane, lane + (1 - y0 + kQLanes - 1 - lane) / kQLanes * kQLanes);
+                const int r_hi = min(kQSH, a.H - y0 + 1);
+                const int gx0 = x0 - 8 + q * 4;
+                if (gx0 >= 0 && gx0 + 4 <= a.W && fits[0] && fits[1] && fits[2] && fits[3]) {
+                    // the common case: four columns inside the frame, all int32-exact
+                    for (int r = r_lo; r < r_hi; r += kQLanes) {
+                        uint2 w = *reinterpret_cast<const uint2*>(&st[r][q * 4]);
+                        const uint32_t x0v = min(w.x & 0xffffu, (uint32_t)M), x1v = min(w.x >> 16, (uint32_t)M);
+                        const uint32_t x2v = min(w.y & 0xffffu, (uint32_t)M), x3v = min(w.y >> 16, (uint32_t)M);
+                        w.x = det_i32(cA[0], cG[0], cO[0], x0v, M) | (det_i32(cA[1], cG[1], cO[1], x1v, M) << 16);
+                        w.y = det_i32(cA[2], cG[2], cO[2], x2v, M) | (det_i32(cA[3], cG[3], cO[3], x3v, M) << 16);
+                        *reinterpret_cast<uint2*>(&st[r][q * 4]) = w;
                     }
-                    w.x = v[0] | (v[1] << 16);
-                    w.y = v[2] | (v[3] << 16);
-                    *reinterpret_cast<uint2*>(&st[r][q * 4]) = w;
+                } else {
+                    for (int r = r_lo; r < r_hi; r += kQLanes) {
+                        uint2 w = *reinterpret_cast<const uint2*>(&st[r][q * 4]);
+                        uint32_t v[4] = {w.x & 0xffffu, w.x >> 16, w.y & 0xffffu, w.y >> 16};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int gx = gx0 + j;
+                            if (gx >= 0 && gx < a.W) {
+                                const uint32_t x = min(v[j], (uint32_t)M);
+                                v[j] = fits[j] ? det_i32(cA[j], cG[j], cO[j], x, M)
+                                               : det_i64(cA[j], cG[j], cO[j], x, M);
+                            }
+                        }
+                        w.x = v[0] | (v[1] << 16);
+                        w.y = v[2] | (v[3] << 16);
+                        *reinterpret_cast<uint2*>(&st[r][q * 4]) = w;
+                    }
                 }
             }
             __syncthreads();
