@@ -186,6 +186,16 @@ LUTC_API int lutc_apply_stretch(const lutc_raster* in, const lutc_coeffs* per_ba
 LUTC_API int lutc_device_status(int* status, lutc_stream stream);
 
 /**
+ * Exercises the kernels' failure path: launches one block that waits on an
+ * mbarrier nothing will complete, with a limit of `wait_cycles` SM clock
+ * cycles (1 .. 2^31) instead of the kernels' ~2 s; the wait gives up, records
+ * LUTC_ETIMEOUT in the status word (see lutc_device_status) and the block
+ * returns.  The device stays usable.  Asynchronous on `stream`; LUTC_EINVAL
+ * for a limit out of range.
+ */
+LUTC_API int lutc_selftest_wait_timeout(long long wait_cycles, lutc_stream stream);
+
+/**
  * Device workspace bytes of lutc_correct_image_host for this raster and flags
  * (0 for an invalid raster or flags): the fused path's tables, a device copy
  * of the raster and a staging area for the output (rows padded to 16 bytes).

@@ -50,14 +50,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
-// Waits for the phase of `bar` with the given parity; false after kWaitCycles, with LUTC_ETIMEOUT
-// recorded in *status (first error wins).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status)
+// Waits for the phase of `bar` with the given parity; false after `limit` cycles (kWaitCycles by
+// default), with LUTC_ETIMEOUT recorded in *status (first error wins).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status,
+                                                  long long limit = kWaitCycles)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > limit) {
             atomicCAS(status, 0, LUTC_ETIMEOUT);
             return false;
         }

@@ -816,6 +816,26 @@ int* device_status_ptr()
 }
 }  // namespace lutc
 
+namespace lutc {
+namespace {
+// one thread waits on a barrier that expects an arrival nobody makes
+__global__ void k_selftest_wait(long long cycles)
+{
+    __shared__ uint64_t bar;
+    ptx::mbar_init(&bar, 1);
+    ptx::fence_mbar_init();
+    ptx::mbar_wait_bounded(&bar, 0, &g_device_status, cycles);
+}
+}  // namespace
+}  // namespace lutc
+
+extern "C" int lutc_selftest_wait_timeout(long long wait_cycles, lutc_stream stream)
+{
+    if (wait_cycles < 1 || wait_cycles > (1ll << 31)) return LUTC_EINVAL;
+    lutc::k_selftest_wait<<<1, 1, 0, (cudaStream_t)stream>>>(wait_cycles);
+    return lutc::cuda_status(cudaGetLastError());
+}
+
 extern "C" int lutc_device_status(int* status, lutc_stream stream)
 {
     if (!status) return LUTC_EINVAL;

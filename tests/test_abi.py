@@ -199,3 +199,9 @@ def test_host_path_workspace_and_rejections():
     assert lib.lutc_correct_image_host(ctypes.byref(r), c, 1, out, 1000, dws, ws - 1, None) == _lib.LUTC_ENOMEM
     assert lib.lutc_correct_image_host(ctypes.byref(r), c, 1, out, 1000, ctypes.c_void_p(0x100010), ws, None) == E
     assert lib.lutc_correct_image_host(ctypes.byref(r), c, 2, out, 1000, dws, ws, None) == E
+
+
+def test_selftest_limit_is_checked_on_the_host():
+    lib = _lib.lib()
+    assert lib.lutc_selftest_wait_timeout(0, None) == _lib.LUTC_EINVAL
+    assert lib.lutc_selftest_wait_timeout((1 << 31) + 1, None) == _lib.LUTC_EINVAL

@@ -8,6 +8,8 @@ columns, unaligned pitches and base pointers (the generic path), DN above
 2^bits - 1, dead columns, constant bands (hi == lo) and columns whose
 response needs 64-bit evaluation.
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -18,6 +20,7 @@ import synth
 pytestmark = pytest.mark.gpu
 
 import paper_1505_05655_gb300 as lutc  # noqa: E402
+from paper_1505_05655_gb300 import _lib  # noqa: E402
 
 
 def dev(a: np.ndarray) -> torch.Tensor:
@@ -299,3 +302,21 @@ def test_every_launch_configuration_is_exact(path, column_threads):
     finally:
         for bits in (10, 12, 14):
             lutc.reset_tuning(bits)
+
+
+def test_a_wait_that_runs_out_is_reported_and_the_device_stays_usable():
+    # a barrier nobody completes, with a limit of 2 M cycles (~1 ms): the wait gives up, records
+    # LUTC_ETIMEOUT in the status word and the block returns
+    lib = lutc.lib()
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    status = ctypes.c_int(-99)
+    assert lib.lutc_device_status(ctypes.byref(status), st) == 0 and status.value == 0
+    assert lib.lutc_selftest_wait_timeout(2_000_000, st) == 0
+    assert lib.lutc_device_status(ctypes.byref(status), st) == 0 and status.value == _lib.LUTC_ETIMEOUT
+    # read-and-clear: the next read is clean, and the device still runs work exactly
+    assert lib.lutc_device_status(ctypes.byref(status), st) == 0 and status.value == 0
+    raw = synth.raster(3, 1, 64, 300, 12)
+    A, G, O = synth.coeff_set(3, 1, 300)
+    d = [torch.from_numpy(a).cuda() for a in (raw, A, G, O)]
+    np.testing.assert_array_equal(lutc.correct_image(*d, 12).cpu().numpy(), oracle.correct_image(raw, A, G, O, 12))
+    assert lib.lutc_selftest_wait_timeout(0, st) == _lib.LUTC_EINVAL
