@@ -62,7 +62,7 @@ typedef struct CUstream_st* lutc_stream;
 enum {
     LUTC_OK = 0,
     LUTC_EINVAL = -1,       /**< an argument is out of range or a pointer is NULL */
-    LUTC_EUNSUPPORTED = -2, /**< valid in principle, not supported by this build */
+    LUTC_EUNSUPPORTED = -2, /**< valid in principle, not supported by this library version */
     LUTC_ENOMEM = -3,       /**< a workspace is too small / device memory exhausted */
     LUTC_ECUDA = -4,        /**< a CUDA call or kernel launch failed */
     LUTC_ETIMEOUT = -5,     /**< a bounded wait expired */
