@@ -5,8 +5,8 @@
  * The paper's framework (Sections I-II) lets a client name a processing task,
  * hand over an input data set with a comma-separated parameter list (matrix
  * dimensions, data type, polynomial orders) and name where the results go;
- * "LUT generation and image correction" is one of the tasks it names
- * (Section I).  Each entry point below is one such task on device memory: the
+ * generating look-up tables and correcting images with them is one of the
+ * tasks it names (Section I).  Each entry point below is one such task on device memory: the
  * caller passes the input, the parameters and the output, the library runs
  * its own CUDA kernels on the caller's stream.
  *
