@@ -102,13 +102,13 @@ LUTC_API int lutc_version(void);
 LUTC_API const char* lutc_strerror(int status);
 
 /**
- * Step (L), Section I's "LUT generation": lut[c][x] = D[c][x] for c < ncols,
+ * Step (L), the LUT generation of Section I: lut[c][x] = D[c][x] for c < ncols,
  * x < 2^bits.  lut: device uint16[ncols][2^bits], written in full.
  */
 LUTC_API int lutc_lutgen(const lutc_coeffs* coeffs, int bits, uint16_t* lut, lutc_stream stream);
 
 /**
- * Step (P), Section I's "image correction" with a materialised LUT:
+ * Step (P), the image correction of Section I with a materialised LUT:
  * out[b][y][c] = lut[b][c][min(in[b][y][c], M)].
  * lut: device uint16[bands][width][2^bits]; out: device uint16 rows of out_pitch_bytes (>= 2 * width).
  */
@@ -152,8 +152,8 @@ LUTC_API size_t lutc_correct_image_workspace(const lutc_raster* in);
 LUTC_API int lutc_correct_image_tables(const lutc_raster* in, size_t* hist_offset, size_t* S_offset, size_t* lohi_offset);
 
 /**
- * The whole correction of a raster without materialising any LUT, Section I's
- * "LUT generation and image correction" as one task.
+ * The whole correction of a raster without materialising any LUT: Section I's
+ * LUT generation and image correction as one task.
  * With LUTC_STRETCH: pass 1 evaluates D on chip and builds every band's
  * histogram (H), a scan builds S and lo/hi (S), pass 2 re-reads the raw
  * raster and writes out8 = S[D[c][raw]] (= steps C and A fused); out is

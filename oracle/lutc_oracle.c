@@ -6,7 +6,7 @@
  * check and the benchmark's CPU-baseline / reference arm may load it; the
  * product path never calls it and shares no code, header or table with it.
  *
- * The paper (Section I) names "LUT generation and image correction" as one of
+ * The paper (Section I) names LUT generation and image correction as one of
  * the compute-heavy tasks its client-server framework ships to a remote GPU,
  * but prints no formula.  The definitions below are the library's, written
  * out directly in exact integer arithmetic (int64; every intermediate is

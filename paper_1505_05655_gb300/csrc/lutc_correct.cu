@@ -1,6 +1,6 @@
 // The fused, table-free correction: lutc_hist and lutc_correct_image.
 //
-// Section I of the paper names "LUT generation and image correction" as one
+// Section I of the paper names LUT generation and image correction as one
 // task a client ships to the GPU server.  Materialising every detector's LUT
 // costs more memory traffic than the image itself at 14 bits (2^14 entries x
 // 2 bytes per column against 2 bytes per pixel of a column), so the fused
