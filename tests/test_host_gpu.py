@@ -23,7 +23,8 @@ def _coeffs(seed, bands, w):
 
 
 @pytest.mark.parametrize("bands,h,w,bits,pad", [(3, 700, 1300, 12, 0), (1, 9000, 6000, 12, 0), (2, 333, 517, 14, 3),
-                                                 (4, 64, 256, 10, 8), (1, 1, 1, 12, 0), (2, 5000, 5000, 12, 1)])
+                                                 (4, 64, 256, 10, 8), (1, 1, 1, 12, 0), (2, 5000, 5000, 12, 1),
+                                                 (2, 300, 700, 16, 0), (1, 1, 20000, 12, 0), (3, 2049, 8, 8, 5)])
 def test_pinned_host_raster(bands, h, w, bits, pad):
     raw = torch.zeros((bands, h, w + pad), dtype=torch.uint16).pin_memory()
     raw[:, :, :w] = torch.from_numpy(synth.raster(3 + bits, bands, h, w, bits, sat_frac=0.001))
