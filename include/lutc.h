@@ -227,6 +227,23 @@ LUTC_API int lutc_correct_image_host(const lutc_raster* in, const lutc_coeffs* p
                                      int64_t out_pitch_bytes, void* workspace, size_t workspace_bytes,
                                      lutc_stream stream);
 
+/** Device workspace bytes of lutc_correct_frames_host for `frames` frames of this shape (two halves when frames > 1). */
+LUTC_API size_t lutc_correct_frames_host_workspace(const lutc_raster* in, int flags, int frames);
+
+/**
+ * lutc_correct_image_host over a sequence of n frames of one sensor: every
+ * frame has in's shape, pitch and bits and the same coefficients; frame f is
+ * read from host memory at frames[f] and written to host memory at outs[f]
+ * (out_pitch_bytes as for lutc_correct_image_host).  Frames alternate two
+ * halves of the workspace, so a frame's copies in overlap the previous
+ * frame's pass 2 and copies out.  Same stream semantics and errors as
+ * lutc_correct_image_host (LUTC_EINVAL for n < 0 or a null frame or output).
+ */
+LUTC_API int lutc_correct_frames_host(const lutc_raster* in, const void* const* frames, int n,
+                                      const lutc_coeffs* per_band, int flags, void* const* outs,
+                                      int64_t out_pitch_bytes, void* workspace, size_t workspace_bytes,
+                                      lutc_stream stream);
+
 /* ------------------------------------------------------------------------
  * The paper's task interface.  A client names a task with a flag, passes a
  * comma-separated parameter list of at most 200 bytes (sizes of the data

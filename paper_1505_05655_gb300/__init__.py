@@ -20,7 +20,7 @@ from . import net  # noqa: E402,F401  (the TCP transport's client side)
 __all__ = ["LutcError", "lib", "version", "lutgen", "apply_u16", "hist", "stretch", "compose", "apply_u8",
            "correct_image_workspace", "correct_image_tables", "correct_image", "apply_stretch", "trace_enable",
            "trace_read", "raster_desc", "coeff_descs", "set_tuning", "reset_tuning", "get_tuning", "Batch",
-           "batch_autotune", "Server", "submit", "fit", "demosaic", "correct_image_host",
+           "batch_autotune", "Server", "submit", "fit", "demosaic", "correct_image_host", "correct_frames_host",
            "net",
            "device_info"]
 
@@ -531,3 +531,40 @@ def correct_image_host(raw: torch.Tensor, A: torch.Tensor, G: torch.Tensor, O: t
     check(lib().lutc_correct_image_host(ctypes.byref(desc), cd, flags, out.data_ptr(), opitch, workspace.data_ptr(),
                                         workspace.numel(), _stream(stream, dev)), "lutc_correct_image_host")
     return out
+
+
+def correct_frames_host(frames, A: torch.Tensor, G: torch.Tensor, O: torch.Tensor, bits: int, stretch: bool = True,
+                        outs=None, workspace: torch.Tensor | None = None, stream=None):
+    """:func:`correct_image_host` over a sequence of same-shape host frames of one sensor, pipelined
+    (a frame's copies in overlap the previous frame's drain).  Synchronises nothing."""
+    if not frames:
+        return []
+    f0 = frames[0]
+    for f in frames:
+        if f.device.type != "cpu" or f.dtype != torch.uint16 or f.shape != f0.shape or f.stride() != f0.stride():
+            raise TypeError("frames must be host (CPU) torch.uint16 tensors of one shape and layout")
+    r3 = f0 if f0.dim() == 3 else f0.unsqueeze(0)
+    bands, h, w = r3.shape
+    if r3.numel() and (r3.stride(2) != 1 or (bands > 1 and h > 0 and r3.stride(0) != h * r3.stride(1))):
+        raise ValueError("frames must be [bands, height, width] with contiguous rows stacked at height * pitch")
+    desc = Raster(r3.data_ptr(), (r3.stride(1) if r3.numel() else w) * 2, w, h, bands, bits)
+    cd = coeff_descs(A, G, O)
+    dev = A.device
+    odt = torch.uint8 if stretch else torch.uint16
+    if outs is None:
+        outs = [torch.empty(r3.shape, dtype=odt, pin_memory=f0.is_pinned()) for _ in frames]
+    o0 = outs[0] if outs[0].dim() == 3 else outs[0].unsqueeze(0)
+    for o in outs:
+        if o.device.type != "cpu" or o.dtype != odt or o.stride() != outs[0].stride() or o.shape != outs[0].shape:
+            raise TypeError("outs must be host (CPU) %s tensors of one shape and layout" % odt)
+    opitch = (o0.stride(1) if o0.numel() else w) * outs[0].element_size()
+    flags = LUTC_STRETCH if stretch else 0
+    n = len(frames)
+    need = int(lib().lutc_correct_frames_host_workspace(ctypes.byref(desc), flags, n))
+    if workspace is None:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    fin = (ctypes.c_void_p * n)(*[f.data_ptr() for f in frames])
+    fout = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    check(lib().lutc_correct_frames_host(ctypes.byref(desc), fin, n, cd, flags, fout, opitch, workspace.data_ptr(),
+                                         workspace.numel(), _stream(stream, dev)), "lutc_correct_frames_host")
+    return outs

@@ -108,6 +108,9 @@ SIGNATURES = {
     "lutc_net_server_stats": (_I, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "lutc_net_server_destroy": (_I, [_P]),
     "lutc_selftest_wait_timeout": (_I, [ctypes.c_longlong, _P]),
+    "lutc_correct_frames_host_workspace": (_SZ, [ctypes.POINTER(Raster), _I, _I]),
+    "lutc_correct_frames_host": (_I, [ctypes.POINTER(Raster), ctypes.POINTER(_P), _I, ctypes.POINTER(Coeffs), _I,
+                                      ctypes.POINTER(_P), _I64, _P, _SZ, _P]),
     "lutc_demosaic": (_I, [ctypes.POINTER(Raster), ctypes.POINTER(Coeffs), _I, _P, _I64, _P]),
     "lutc_batch_workspace": (_SZ, [ctypes.POINTER(Job), _I]),
     "lutc_server_create": (_I, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]),

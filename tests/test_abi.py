@@ -205,3 +205,23 @@ def test_selftest_limit_is_checked_on_the_host():
     lib = _lib.lib()
     assert lib.lutc_selftest_wait_timeout(0, None) == _lib.LUTC_EINVAL
     assert lib.lutc_selftest_wait_timeout((1 << 31) + 1, None) == _lib.LUTC_EINVAL
+
+
+def test_frames_host_rejections():
+    lib = _lib.lib()
+    r = _raster(bands=2, width=1000, height=50, pitch_bytes=2000)
+    one = lib.lutc_correct_image_host_workspace(ctypes.byref(r), 1)
+    assert lib.lutc_correct_frames_host_workspace(ctypes.byref(r), 1, 1) == one
+    assert lib.lutc_correct_frames_host_workspace(ctypes.byref(r), 1, 7) == 2 * one
+    assert lib.lutc_correct_frames_host_workspace(ctypes.byref(r), 1, 0) == 0
+    c = (Coeffs * 2)(*[Coeffs(0x20000, 0x30000, 0x40000, 1000)] * 2)
+    fr = (ctypes.c_void_p * 3)(0x100000, 0x200000, 0x300000)
+    outs = (ctypes.c_void_p * 3)(0x400000, 0x500000, 0x600000)
+    E = _lib.LUTC_EINVAL
+    ws = ctypes.c_void_p(0x1000000)
+    assert lib.lutc_correct_frames_host(ctypes.byref(r), fr, -1, c, 1, outs, 1000, ws, 2 * one, None) == E
+    assert lib.lutc_correct_frames_host(ctypes.byref(r), None, 3, c, 1, outs, 1000, ws, 2 * one, None) == E
+    bad = (ctypes.c_void_p * 3)(0x100000, 0, 0x300000)
+    assert lib.lutc_correct_frames_host(ctypes.byref(r), bad, 3, c, 1, outs, 1000, ws, 2 * one, None) == E
+    assert lib.lutc_correct_frames_host(ctypes.byref(r), fr, 3, c, 1, outs, 1000, ws, one, None) == _lib.LUTC_ENOMEM
+    assert lib.lutc_correct_frames_host(ctypes.byref(r), fr, 0, c, 1, outs, 1000, ws, 0, None) == 0

@@ -70,3 +70,22 @@ def test_small_workspace_is_refused():
     with pytest.raises(lutc.LutcError) as e:
         lutc.correct_image_host(raw, *d, 12, workspace=torch.empty(1024, dtype=torch.uint8, device="cuda"))
     assert e.value.status == _lib.LUTC_ENOMEM
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5])
+def test_frame_sequences_equal_single_calls(n):
+    bands, h, w, bits = 2, 1100, 3000, 12
+    A, G, O, d = _coeffs(17, bands, w)
+    frames = [torch.from_numpy(synth.raster(30 + k, bands, h, w, bits)).pin_memory() for k in range(n)]
+    outs = lutc.correct_frames_host(frames, *d, bits)
+    torch.cuda.synchronize()
+    for f, o in zip(frames, outs):
+        assert torch.equal(o, lutc.correct_image(f.cuda(), *d, bits).cpu())
+    # detector only, padded rows (strided copies), frames from pageable memory
+    frames = [torch.zeros((bands, h, w + 5), dtype=torch.uint16)[:, :, :w] for _ in range(n)]
+    for k, f in enumerate(frames):
+        f.copy_(torch.from_numpy(synth.raster(40 + k, bands, h, w, bits)))
+    outs = lutc.correct_frames_host(frames, *d, bits, stretch=False)
+    torch.cuda.synchronize()
+    for f, o in zip(frames, outs):
+        assert torch.equal(o, lutc.correct_image(f.contiguous().cuda(), *d, bits, stretch=False).cpu())
