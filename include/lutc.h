@@ -475,8 +475,11 @@ LUTC_API int lutc_batch_autotune(const lutc_job* jobs, int n, void* workspace, s
  * the result back).  Requests are queued, admitted against a device-memory
  * budget, grouped into batches of up to max_batch requests or max_wait_us,
  * and run as overlapping batches on up to `streams` CUDA streams while new
- * requests keep arriving (continuous batching).  Each sensor's coefficients
- * are uploaded to the device on its first request and cached.
+ * requests keep arriving (continuous batching).  A request that arrives while
+ * no batch is on the device launches at once (waiting would only add
+ * latency); requests that arrive while batches run accumulate until a batch
+ * is full, the window ends, or the device goes idle.  Each sensor's
+ * coefficients are uploaded to the device on its first request and cached.
  * ------------------------------------------------------------------------ */
 
 /** Server configuration; zero fields take the defaults in brackets. */
@@ -489,6 +492,7 @@ typedef struct {
     int32_t fake_device;  /**< test facility: 1 = run no CUDA at all; a batch "completes" fake_latency_us after launch */
     int32_t fake_latency_us;
     int32_t fail_every;   /**< test facility: when > 0, every fail_every-th batch is failed on the host with LUTC_ECUDA */
+    int32_t hold_when_idle; /**< 1: every batch waits out its window even on an idle device; 0 [default]: launch at once when idle */
 } lutc_server_config;
 
 /** Request flags. */

@@ -339,10 +339,11 @@ class Server:
     """
 
     def __init__(self, budget_bytes: int = 0, max_batch: int = 0, max_wait_us: int = 0, streams: int = 0,
-                 max_queue: int = 0, fake_device: bool = False, fake_latency_us: int = 0, fail_every: int = 0):
+                 max_queue: int = 0, fake_device: bool = False, fake_latency_us: int = 0, fail_every: int = 0,
+                 hold_when_idle: bool = False):
         from ._lib import ServerConfig
         self.cfg = ServerConfig(budget_bytes, max_batch, max_wait_us, streams, max_queue, int(fake_device),
-                                fake_latency_us, fail_every)
+                                fake_latency_us, fail_every, int(hold_when_idle))
         self._h = ctypes.c_void_p()
         self._keep = {}
         check(lib().lutc_server_create(ctypes.byref(self.cfg), ctypes.byref(self._h)), "lutc_server_create")

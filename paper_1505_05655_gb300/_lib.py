@@ -49,7 +49,7 @@ class Tuning(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int32), ("max_wait_us", ctypes.c_int32),
                 ("streams", ctypes.c_int32), ("max_queue", ctypes.c_int32), ("fake_device", ctypes.c_int32),
-                ("fake_latency_us", ctypes.c_int32), ("fail_every", ctypes.c_int32)]
+                ("fake_latency_us", ctypes.c_int32), ("fail_every", ctypes.c_int32), ("hold_when_idle", ctypes.c_int32)]
 
 
 class RequestInfo(ctypes.Structure):

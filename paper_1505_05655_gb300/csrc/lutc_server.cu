@@ -324,9 +324,10 @@ void lutc_server_st::run_batcher()
     for (;;) {
         cv_batcher.wait(lk, [&] { return stop || !pending.empty(); });
         if (stop) return;
-        // the batch window: full, or the oldest request has waited max_wait_us
+        // the batch window: full, the oldest request has waited max_wait_us, or nothing is on the
+        // device (the completer wakes this thread when a batch finishes)
         const double deadline = pending.front()->t_submit + cfg.max_wait_us * 1e-6;
-        while (!stop && (int)pending.size() < cfg.max_batch) {
+        while (!stop && (int)pending.size() < cfg.max_batch && (cfg.hold_when_idle || !flights.empty())) {
             const double left = deadline - now_s();
             if (left <= 0) break;
             cv_batcher.wait_for(lk, std::chrono::duration<double>(left));
@@ -501,7 +502,9 @@ extern "C" int lutc_server_create(const lutc_server_config* config, lutc_server*
     if (c.max_wait_us <= 0) c.max_wait_us = 2000;
     if (c.streams <= 0) c.streams = 3;
     if (c.max_queue <= 0) c.max_queue = 4096;
-    if (c.max_batch > 4096 || c.streams > 64 || c.fake_latency_us < 0 || c.fail_every < 0) return LUTC_EINVAL;
+    if (c.max_batch > 4096 || c.streams > 64 || c.fake_latency_us < 0 || c.fail_every < 0 ||
+        (c.hold_when_idle != 0 && c.hold_when_idle != 1))
+        return LUTC_EINVAL;
     lutc_server s = new (std::nothrow) lutc_server_st();
     if (!s) return LUTC_ENOMEM;
     s->cfg = c;

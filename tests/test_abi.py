@@ -225,3 +225,41 @@ def test_frames_host_rejections():
     assert lib.lutc_correct_frames_host(ctypes.byref(r), bad, 3, c, 1, outs, 1000, ws, 2 * one, None) == E
     assert lib.lutc_correct_frames_host(ctypes.byref(r), fr, 3, c, 1, outs, 1000, ws, one, None) == _lib.LUTC_ENOMEM
     assert lib.lutc_correct_frames_host(ctypes.byref(r), fr, 0, c, 1, outs, 1000, ws, 0, None) == 0
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct of the header has the size and field offsets of its ctypes twin (compiled with the
+    host C compiler against the header itself)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    twins = {"lutc_coeffs": _lib.Coeffs, "lutc_raster": _lib.Raster, "lutc_job": _lib.Job,
+             "lutc_batch_config": _lib.BatchConfig, "lutc_server_config": _lib.ServerConfig,
+             "lutc_request_info": _lib.RequestInfo, "lutc_tuning": _lib.Tuning}
+    text = open(HEADER).read()
+    assert set(re.findall(r"^\}\s*(lutc_\w+)\s*;", text, flags=re.M)) == set(twins), "a struct has no ctypes twin"
+    c_name = {"in_": "in"}
+    # field names in declaration order (padding would hide a missing trailing field from sizeof)
+    for body, name in re.findall(r"typedef struct \{(.*?)\}\s*(lutc_\w+)\s*;", text, flags=re.S):
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        fields = re.findall(r"(\w+)\s*;", body)
+        assert fields == [c_name.get(f, f) for f, _ in twins[name]._fields_], name
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "lutc.h"', "int main(void) {"]
+    for name, py in twins.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for f, _ in py._fields_:
+            cf = c_name.get(f, f)
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, f, name, cf))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                         text=True).stdout.splitlines())
+    for name, py in twins.items():
+        assert int(got[name]) == ctypes.sizeof(py), name
+        for f, _ in py._fields_:
+            assert int(got["%s.%s" % (name, f)]) == getattr(py, f).offset, (name, f)

@@ -34,7 +34,8 @@ def _expected(p, h):
 
 
 def test_result_is_the_same_alone_and_in_a_mix():
-    server = lutc.Server(budget_bytes=2 << 30, max_batch=8, max_wait_us=3000, streams=3)
+    # batches wait out their window even on an idle device, so that the target lands in a mix
+    server = lutc.Server(budget_bytes=2 << 30, max_batch=8, max_wait_us=3000, streams=3, hold_when_idle=True)
     pool = _setup(server)
     target = (2, 333)  # sensor, rows
     p = pool[target[0]]

@@ -48,7 +48,7 @@ def test_requests_complete_and_batch_up():
 
 
 def test_window_holds_a_lone_request_then_launches_it():
-    s = _server(max_batch=32, max_wait_us=60000, fake_latency_us=100)
+    s = _server(max_batch=32, max_wait_us=60000, fake_latency_us=100, hold_when_idle=True)
     raw, out = _bufs(8)
     t0 = time.perf_counter()
     info = s.wait(s.submit(0, raw, out))
@@ -61,6 +61,39 @@ def test_window_holds_a_lone_request_then_launches_it():
     infos = [s.wait(t) for t in ts]
     assert max(i.start_s - i.submit_s for i in infos) < 0.05
     s.close()
+
+
+def test_idle_device_launches_a_lone_request_at_once():
+    s = _server(max_batch=32, max_wait_us=200000, fake_latency_us=100)
+    for _ in range(3):
+        info = s.wait(s.submit(0, *_bufs(8)))
+        assert info.status == 0 and info.batch_size == 1
+        assert info.start_s - info.submit_s < 0.05  # far inside the 200 ms window
+    s.close()
+
+
+def test_requests_accumulate_while_a_batch_runs_and_launch_when_it_ends():
+    # the first request launches at once (idle device) and runs 150 ms; the next ones wait for it
+    # to finish, not for their 2 s window, and go as one batch
+    s = _server(max_batch=32, max_wait_us=2000000, fake_latency_us=150000, streams=3)
+    first = s.submit(0, *_bufs(8))
+    time.sleep(0.02)
+    rest = [s.submit(k % 4, *_bufs(8)) for k in range(6)]
+    i0 = s.wait(first)
+    infos = [s.wait(t) for t in rest]
+    assert i0.batch_size == 1 and all(i.status == 0 for i in infos)
+    assert all(i.batch_size == 6 for i in infos)
+    assert min(i.start_s for i in infos) >= i0.done_s - 0.005  # formed when the device went idle
+    assert max(i.start_s - i.submit_s for i in infos) < 1.0  # well before the window's end
+    assert s.stats()["batches"] == 2
+    s.close()
+
+
+def test_server_config_is_checked():
+    with pytest.raises(lutc.LutcError):
+        lutc.Server(fake_device=True, hold_when_idle=2)
+    with pytest.raises(lutc.LutcError):
+        lutc.Server(fake_device=True, streams=65)
 
 
 def test_first_request_of_a_sensor_is_the_cache_miss():
