@@ -59,7 +59,7 @@ TRAFFIC_SOURCES = {
 
 def csrc_hash(workload: str) -> str:
     h = hashlib.sha256()
-    for rel in TRAFFIC_SOURCES[workload]:
+    for rel in TRAFFIC_SOURCES[workload.split("/")[0]]:
         with open(os.path.join(ROOT, "paper_1505_05655_gb300", rel), "rb") as f:
             h.update(rel.encode())
             h.update(f.read())
@@ -555,15 +555,16 @@ def run_batch(args):
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
-    ims = synth.batch_images(synth.BATCH_SEED + 7 * rank, n=args.batch_images)
+    align = args.row_align  # bytes; rows of every input (uint16) and output (uint8) padded to a multiple
+    ims = synth.batch_images(synth.BATCH_SEED + 7 * rank, n=args.batch_images, pitch_multiple=align // 2)
     pixels = sum(im["bands"] * im["height"] * im["width"] for im in ims)
     host_in = [torch.from_numpy(im["raw"]).pin_memory() for im in ims]
     dev_in = [h.to(device) for h in host_in]
     images = []
     for im, d in zip(ims, dev_in):
         A, G, O = (torch.from_numpy(a).to(device) for a in (im["A"], im["G"], im["O"]))
-        # output rows padded to 16 bytes like the input rows, so every row takes vector stores
-        opitch = -(-im["width"] // 16) * 16
+        # output rows padded like the input rows, so every row takes vector stores
+        opitch = -(-im["width"] // align) * align
         out = torch.empty((im["bands"], im["height"], opitch), dtype=torch.uint8, device=device)[:, :, :im["width"]]
         images.append((d[:, :, :im["width"]], A, G, O, im["bits"], out, True))
     stream = torch.cuda.current_stream(device)
@@ -631,13 +632,14 @@ def run_batch(args):
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": "batch: %d images, W log-uniform 512-8192, H log-uniform 256-8192, bits "
                                    "{10,12,14}, bands {1,3,4}, full pipeline, uint8 out" % len(ims),
-                       "images": len(ims), "pixels_per_step": pixels,
+                       "images": len(ims), "pixels_per_step": pixels, "row_align_bytes": align,
                        "l2": "inputs larger than L2 (%.2f GB read per step)" % (2 * pixels / 1e9),
                        "autotuned": {"column_threads": cfg.column_threads, "blocks_per_sm": cfg.blocks_per_sm,
                                      "graph": True, "tuning_ms": tune_ms}},
             "hbm_frac_step": 5 * pixels / (ms * 1e-3) / 1e9 / peak,
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                         "traffic": ncu_traffic(["pass1", "", "pass2"][dom], "batch", pixels),
+                         "traffic": ncu_traffic(["pass1", "", "pass2"][dom],
+                                                "batch" if align == 16 else "batch/align%d" % align, pixels),
                          "kernel": ["pass1 k_tma_strip<hist, batch>", "", "pass2 k_tma_strip<apply, batch>"][dom],
                          "peak_source": peak_src + " (copy bandwidth)", "alg_bytes_per_launch": alg[dom]},
             "phases_ms": {"pass1_hist": avg[0], "scan": avg[1], "pass2_apply": avg[2]},
@@ -692,12 +694,12 @@ def run_serve(args):
         _, hs, _, _ = synth.batch_spec(synth.SERVE_SEED + 1 + sid, pool_per_sensor)
         for k in range(pool_per_sensor):
             H = int(hs[k])
-            # rows padded to 16 bytes (the TMA path's alignment), bands stacked at H x pitch
-            pitch = -(-W // 8) * 8
+            # rows padded to args.row_align bytes (at least the TMA path's 16), bands stacked at H x pitch
+            pitch = -(-W // (args.row_align // 2)) * (args.row_align // 2)
             host = np.zeros((B, H, pitch), np.uint16)
             synth.raster(synth.batch_image_seed(synth.SERVE_SEED + 100 + sid, k), B, H, W, Bt, out=host[:, :, :W])
             raw = torch.from_numpy(host).to(device)[:, :, :W]
-            opitch = -(-W // 16) * 16
+            opitch = -(-W // args.row_align) * args.row_align
             out = torch.empty((B, H, opitch), dtype=torch.uint8, device=device)[:, :, :W]
             pool.append((sid, raw, out, B * H * W))
             if (sid * pool_per_sensor + k) % 16 == 0:
@@ -802,7 +804,7 @@ def run_serve(args):
             "config": {"workload": "serve: %d sensors from the batch mixture, %d pool rasters each, device-resident; "
                                    "Poisson arrivals 50/200/800 req/s; budget 40 GiB; a request launches at once on "
                                    "an idle device, else batches <= 32 requests or 2 ms, 3 streams"
-                                   % (nsens, pool_per_sensor),
+                                   % (nsens, pool_per_sensor), "row_align_bytes": args.row_align,
                        "l2": "inputs larger than L2 (pool %.1f GB)" % (sum(p_[3] for p_ in pool) * 2 / 1e9)},
             "latency": loads, "saturation": sat, "warmup_with_cache_misses": warm, "server": st,
             "outputs_equal_single_calls": exact,
@@ -999,6 +1001,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--batch-images", type=int, default=256, help="images in the batch workload")
     ap.add_argument("--no-tune", action="store_true", help="batch workload: automatic configuration, no autotuner")
+    ap.add_argument("--row-align", type=int, default=128, choices=[16, 32, 64, 128, 256, 512],
+                    help="batch and serve workloads: bytes every image row is padded to (input and output)")
     ap.add_argument("--quick", action="store_true", help="scene line only (no batch and serving summaries)")
     ap.add_argument("--cases", default="", help="fit / demosaic workloads: run only the cases whose name contains "
                                                   "one of these comma-separated words ('_' stands for a space)")
