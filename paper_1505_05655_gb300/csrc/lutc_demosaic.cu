@@ -258,12 +258,18 @@ constexpr int kQStages = 2;
 constexpr int kQStageElems = (kQSW * kQSH + 63) / 64 * 64;  // stages 128-byte aligned
 constexpr uint32_t kQBoxBytes = kQSW * kQSH * 2;
 constexpr int kQLanes = kQThreads / (kQSW / 4);             // correction: row lanes of 36 x 4 columns
+// a staged coefficient row: kQSW int32 padded so that every row of every stage starts on the
+// 128-byte boundary a tiled tensor copy writes to
+constexpr int kQCoefRow = (kQSW * 4 + 127) / 128 * 128 / 4;
 static_assert(kQThreads == 256 && kQLanes >= 1, "tile geometry");
+static_assert((kQStageElems * 2) % 128 == 0 && (kQCoefRow * 4) % 128 == 0, "TMA destinations 128-byte aligned");
 
 struct DemosaicTmaArgs {
-    CUtensorMap map;   // uint16 [H][W], row stride = pitch, box {kQSW, kQSH}
+    CUtensorMap map;      // uint16 [H][W], row stride = pitch, box {kQSW, kQSH}
+    CUtensorMap cmap[3];  // int32 [W] coefficient rows A, G, O, box {kQSW} (when coef_tma)
     int W, H, bits;
-    BandCoef coef;     // A == nullptr: no correction
+    BandCoef coef;        // A == nullptr: no correction
+    int coef_tma;         // 1: each tile's load also brings its columns' coefficients into the stage
     uint8_t* out;
     int64_t out_pitch;
     int vout;
@@ -272,42 +278,74 @@ struct DemosaicTmaArgs {
     int* status;       // the library's kernel status word
 };
 
+// Tile k of a block is tile k x step + first in row-major order over `strips` tiles per row; the
+// cursor walks them with one compare per step instead of a 64-bit division.
+struct TileCursor {
+    int tx, dtx, strips;
+    int ty, dty;
+    __device__ __forceinline__ void start(int64_t first, int64_t step, int s)
+    {
+        strips = s;
+        ty = (int)(first / s);
+        tx = (int)(first - (int64_t)ty * s);
+        dty = (int)(step / s);
+        dtx = (int)(step - (int64_t)dty * s);
+    }
+    __device__ __forceinline__ void next()
+    {
+        tx += dtx;
+        ty += dty;
+        if (tx >= strips) {
+            tx -= strips;
+            ++ty;
+        }
+    }
+};
+
 template <int PY, int PX, bool kCorrect>
 __global__ void __launch_bounds__(kQThreads, 3) k_demosaic_tma(const __grid_constant__ DemosaicTmaArgs a)
 {
     __shared__ __align__(128) uint16_t ring[kQStages][kQStageElems];
+    __shared__ __align__(128) int32_t cbuf[kCorrect ? kQStages : 1][3][kCorrect ? kQCoefRow : 4];
     __shared__ __align__(8) uint64_t full[kQStages];
     const int tid = threadIdx.x;
     const int64_t n = (int64_t)blockIdx.x < a.ntiles ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     if (n == 0) return;  // the whole block, before any barrier exists
+    // every tensor copy of this kernel writes to a 128-byte boundary (offsets checked at compile
+    // time); a base off that boundary is refused before any copy is issued
+    if ((ptx::smem_addr(&ring[0][0]) | ptx::smem_addr(&cbuf[0][0][0])) & 127u) {
+        if (tid == 0) atomicCAS(a.status, 0, LUTC_ECUDA);
+        return;
+    }
     if (tid == 0) {
         for (int s = 0; s < kQStages; ++s) ptx::mbar_init(&full[s], 1);
         ptx::fence_mbar_init();
     }
     __syncthreads();
-    auto tile_of = [&](int64_t k, int* x0, int* y0) {
-        const int64_t t = k * gridDim.x + blockIdx.x;
-        const int64_t ty = t / a.strips;
-        *x0 = (int)(t - ty * a.strips) * kQW;
-        *y0 = (int)ty * kQH;
-    };
-    auto issue = [&](int64_t k) {  // thread 0: the block's k-th tile into stage k % kQStages
-        int x0, y0;
-        tile_of(k, &x0, &y0);
-        uint64_t* bar = &full[k % kQStages];
-        ptx::mbar_arrive_expect_tx(bar, kQBoxBytes);
-        ptx::tma_load_2d(ring[k % kQStages], &a.map, bar, x0 - 8, y0 - 1);
+    TileCursor cur, icur;  // the tile being computed; the next tile to load (thread 0)
+    cur.start(blockIdx.x, gridDim.x, a.strips);
+    icur = cur;
+    const bool ctma = kCorrect && a.coef_tma;
+    auto issue = [&](int64_t k) {  // thread 0: the block's k-th tile (icur) into stage k % kQStages
+        const int s = (int)(k % kQStages);
+        uint64_t* bar = &full[s];
+        const int x = icur.tx * kQW - 8;  // a multiple of 8 columns: 16-byte aligned for both maps
+        ptx::mbar_arrive_expect_tx(bar, kQBoxBytes + (ctma ? 3u * kQSW * 4u : 0u));
+        ptx::tma_load_2d(ring[s], &a.map, bar, x, icur.ty * kQH - 1);
+        if (kCorrect && ctma)
+            for (int c = 0; c < 3; ++c) ptx::tma_load_1d(cbuf[s][c], &a.cmap[c], bar, x);
+        icur.next();
     };
     if (tid == 0)
         for (int64_t k = 0; k < n && k < kQStages; ++k) issue(k);
 
     const int32_t M = (1 << a.bits) - 1;
+    const uint32_t M2 = (uint32_t)M | ((uint32_t)M << 16);
     const int q = tid % (kQSW / 4), lane = tid / (kQSW / 4);
     int64_t k = 0;
-    for (; k < n; ++k) {
+    for (; k < n; ++k, cur.next()) {
         const int s = (int)(k % kQStages);
-        int x0, y0;
-        tile_of(k, &x0, &y0);
+        const int x0 = cur.tx * kQW, y0 = cur.ty * kQH;
         const bool ok = ptx::mbar_wait_bounded(&full[s], (uint32_t)((k / kQStages) & 1), a.status);
         if (!__syncthreads_and(ok)) break;  // the same decision in every thread
         uint16_t (*st)[kQSW] = reinterpret_cast<uint16_t (*)[kQSW]>(ring[s]);
@@ -315,13 +353,26 @@ __global__ void __launch_bounds__(kQThreads, 3) k_demosaic_tma(const __grid_cons
             if (lane < kQLanes) {
                 int32_t cA[4], cG[4], cO[4];
                 bool fits[4];
+                if (ctma) {
+                    // staged with the tile (zeros outside the frame)
+                    const int4 va = *reinterpret_cast<const int4*>(&cbuf[s][0][q * 4]);
+                    const int4 vg = *reinterpret_cast<const int4*>(&cbuf[s][1][q * 4]);
+                    const int4 vo = *reinterpret_cast<const int4*>(&cbuf[s][2][q * 4]);
+                    cA[0] = va.x; cA[1] = va.y; cA[2] = va.z; cA[3] = va.w;
+                    cG[0] = vg.x; cG[1] = vg.y; cG[2] = vg.z; cG[3] = vg.w;
+                    cO[0] = vo.x; cO[1] = vo.y; cO[2] = vo.z; cO[3] = vo.w;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int gx = x0 - 8 + q * 4 + j;
+                        const bool in = gx >= 0 && gx < a.W;
+                        cA[j] = in ? __ldg(a.coef.A + gx) : 0;
+                        cG[j] = in ? __ldg(a.coef.G + gx) : 0;
+                        cO[j] = in ? __ldg(a.coef.O + gx) : 0;
+                    }
+                }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const int gx = x0 - 8 + q * 4 + j;
-                    const bool in = gx >= 0 && gx < a.W;
-                    cA[j] = in ? __ldg(a.coef.A + gx) : 0;
-                    cG[j] = in ? __ldg(a.coef.G + gx) : 0;
-                    cO[j] = in ? __ldg(a.coef.O + gx) : 0;
                     fits[j] = col_fits_i32(cA[j], cG[j], cO[j], M);
                     if (fits[j]) cO[j] += 32768;
                 }
@@ -330,14 +381,27 @@ __global__ void __launch_bounds__(kQThreads, 3) k_demosaic_tma(const __grid_cons
                 const int r_hi = min(kQSH, a.H - y0 + 1);
                 const int gx0 = x0 - 8 + q * 4;
                 if (gx0 >= 0 && gx0 + 4 <= a.W && fits[0] && fits[1] && fits[2] && fits[3]) {
-                    // the common case: four columns inside the frame, all int32-exact
-                    for (int r = r_lo; r < r_hi; r += kQLanes) {
-                        uint2 w = *reinterpret_cast<const uint2*>(&st[r][q * 4]);
-                        const uint32_t x0v = min(w.x & 0xffffu, (uint32_t)M), x1v = min(w.x >> 16, (uint32_t)M);
-                        const uint32_t x2v = min(w.y & 0xffffu, (uint32_t)M), x3v = min(w.y >> 16, (uint32_t)M);
+                    // the common case: four columns inside the frame, all int32-exact; two rows per
+                    // step, so eight independent evaluations are in flight
+                    auto correct4 = [&](uint2 w) {
+                        w.x = __vminu2(w.x, M2);  // both halves clamped to M at once
+                        w.y = __vminu2(w.y, M2);
+                        const uint32_t x0v = w.x & 0xffffu, x1v = w.x >> 16, x2v = w.y & 0xffffu, x3v = w.y >> 16;
                         w.x = det_i32(cA[0], cG[0], cO[0], x0v, M) | (det_i32(cA[1], cG[1], cO[1], x1v, M) << 16);
                         w.y = det_i32(cA[2], cG[2], cO[2], x2v, M) | (det_i32(cA[3], cG[3], cO[3], x3v, M) << 16);
-                        *reinterpret_cast<uint2*>(&st[r][q * 4]) = w;
+                        return w;
+                    };
+                    int r = r_lo;
+                    for (; r + kQLanes < r_hi; r += 2 * kQLanes) {
+                        uint2* p0 = reinterpret_cast<uint2*>(&st[r][q * 4]);
+                        uint2* p1 = reinterpret_cast<uint2*>(&st[r + kQLanes][q * 4]);
+                        const uint2 w0 = *p0, w1 = *p1;
+                        *p0 = correct4(w0);
+                        *p1 = correct4(w1);
+                    }
+                    if (r < r_hi) {
+                        uint2* p0 = reinterpret_cast<uint2*>(&st[r][q * 4]);
+                        *p0 = correct4(*p0);
                     }
                 } else {
                     for (int r = r_lo; r < r_hi; r += kQLanes) {
@@ -461,6 +525,19 @@ extern "C" int lutc_demosaic(const lutc_raster* in, const lutc_coeffs* coeffs, i
             t.H = in->height;
             t.bits = in->bits;
             t.coef = a.coef;
+            // coefficient rows as 1-D tensors (their base must be 16-byte aligned); else per-tile loads
+            auto coef_map = [&](CUtensorMap* m, const int32_t* p) {
+                const cuuint64_t d1[1] = {(cuuint64_t)in->width};
+                const cuuint64_t s1[1] = {(cuuint64_t)in->width * 4};  // unused at rank 1
+                const cuuint32_t b1[1] = {(cuuint32_t)kQSW};
+                const cuuint32_t e1[1] = {1};
+                return ((uintptr_t)p % 16) == 0 &&
+                       enc(m, CU_TENSOR_MAP_DATA_TYPE_INT32, 1, const_cast<int32_t*>(p), d1, s1, b1, e1,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+            };
+            t.coef_tma = coeffs && coef_map(&t.cmap[0], coeffs->A) && coef_map(&t.cmap[1], coeffs->G) &&
+                         coef_map(&t.cmap[2], coeffs->O);
             t.out = a.out;
             t.out_pitch = a.out_pitch;
             t.vout = a.vout;

@@ -26,20 +26,23 @@ namespace lutc {
 // ---------------------------------------------------------------------------
 __host__ __device__ inline bool col_fits_i32(int32_t A, int32_t G, int32_t O, int32_t M)
 {
-    const uint64_t m = (uint64_t)M;
-    const uint64_t a = (uint64_t)(A < 0 ? -(int64_t)A : (int64_t)A);
-    const uint64_t g = (uint64_t)(G < 0 ? -(int64_t)G : (int64_t)G);
+    // |A| M^2 + |G| M + |O + 2^15| < 2^31, exactly: M <= 2^16 - 1 makes M^2 a uint32, |A| and |G| are
+    // at most 2^31, so each product is one 32 x 32 -> 64-bit multiply and the sum stays below 2^64
+    const uint32_t mm = (uint32_t)M * (uint32_t)M;
+    const uint32_t a = A < 0 ? 0u - (uint32_t)A : (uint32_t)A;
+    const uint32_t g = G < 0 ? 0u - (uint32_t)G : (uint32_t)G;
     const int64_t o64 = (int64_t)O + 32768;
     const uint64_t o = (uint64_t)(o64 < 0 ? -o64 : o64);
-    return a * (m * m) + g * m + o < ((uint64_t)1 << 31);
+    return (uint64_t)a * mm + (uint64_t)g * (uint32_t)M + o < ((uint64_t)1 << 31);
 }
 
-// int32-exact column; Op = O + 2^15 (fits int32 for such a column)
+// int32-exact column; Op = O + 2^15 (fits int32 for such a column).  Horner form in wrap-around
+// 32-bit arithmetic: (A x + G) x + Op equals A x^2 + G x + Op modulo 2^32, and the true value fits
+// int32, so the 32-bit result is exact.  Then clamp(floor(t / 2^16), 0, M) (arithmetic shift).
 __device__ __forceinline__ uint32_t det_i32(int32_t A, int32_t G, int32_t Op, uint32_t x, int32_t M)
 {
-    const uint32_t t = (uint32_t)A * (x * x) + (uint32_t)G * x + (uint32_t)Op;
-    const int32_t s = ((int32_t)t) >> 16;  // arithmetic shift: floor division by 2^16
-    return (uint32_t)min(max(s, 0), M);
+    const uint32_t t = ((uint32_t)A * x + (uint32_t)G) * x + (uint32_t)Op;
+    return (uint32_t)__vimin_s32_relu(((int32_t)t) >> 16, M);
 }
 
 __device__ __forceinline__ uint32_t det_i64(int32_t A, int32_t G, int32_t O, uint32_t x, int32_t M)

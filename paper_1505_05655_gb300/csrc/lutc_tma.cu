@@ -128,13 +128,6 @@ __device__ __forceinline__ bool consumer_sync(uint64_t* bar, uint32_t& phase)
 // ---------------------------------------------------------------------------
 // per-pixel arithmetic
 // ---------------------------------------------------------------------------
-// (L) in wrap-around int32, Horner form; exact for an int32-exact column (Op = O + 2^15)
-__device__ __forceinline__ uint32_t det_horner(int32_t A, int32_t G, int32_t Op, uint32_t x, int32_t M)
-{
-    const uint32_t t = ((uint32_t)A * x + (uint32_t)G) * x + (uint32_t)Op;
-    return (uint32_t)__vimin_s32_relu(((int32_t)t) >> 16, M);  // clamp(floor(t / 2^16), 0, M)
-}
-
 // (P) clamp of raw DN to M, two pixels per 32-bit word
 __device__ __forceinline__ void unpack_clamped(const uint4 v, uint32_t M2, uint32_t (&x)[8])
 {
@@ -196,7 +189,7 @@ __device__ __forceinline__ void row8(const uint4 v, int n, const int32_t (&A)[8]
     uint32_t x[8], d[8];
     unpack_clamped(v, M2, x);
 #pragma unroll
-    for (int jj = 0; jj < 8; ++jj) d[jj] = det_horner(A[jj], G[jj], O[jj], x[jj], M);
+    for (int jj = 0; jj < 8; ++jj) d[jj] = det_i32(A[jj], G[jj], O[jj], x[jj], M);  // (L)
     if (MODE == kModeHist) {
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj)

@@ -2,7 +2,8 @@
 
 Integer arithmetic throughout: tolerance zero.  Shapes span several 128 x 32
 tiles with ragged right and bottom edges, tiles whose halo leaves the image,
-degenerate images one pixel wide or high, unaligned rows on both sides, all
+degenerate images one pixel wide or high, unaligned rows on both sides, coefficient
+rows off a 16-byte boundary (no TMA staging of the coefficients), all
 four CFA patterns, with and without the fused detector correction (int32 and
 int64 columns), the paper's 2048 x 2048 16-bit frame in full and a frame
 larger than L2 on sampled row bands.
@@ -97,6 +98,26 @@ def test_unaligned_rows(in_off, pad, out_pad):
     for coeffs in (None, (A, G, O)):
         got = _gpu(img, w, "grbg", 12, coeffs, in_off=in_off, out_pad=out_pad)
         np.testing.assert_array_equal(got, _ref(img, w, "grbg", 12, coeffs))
+
+
+@pytest.mark.parametrize("coef_off", [1, 2, 3])
+def test_unaligned_coefficient_rows(coef_off):
+    # aligned raster rows (tiles through TMA) but coefficient rows 4 bytes off a 16-byte boundary:
+    # the coefficients cannot travel with the tiles and are loaded per tile instead
+    h, w, bits = 67, 304, 12
+    img = _raw(9 + coef_off, h, w, bits)
+    A, G, O = synth.coeffs(9 + coef_off, 0, w)
+    A[::29] = 900  # int64 columns
+
+    def shifted(a):
+        buf = torch.zeros(w + 4, dtype=torch.int32, device="cuda")
+        buf[coef_off:coef_off + w] = torch.from_numpy(a).cuda()
+        return buf[coef_off:coef_off + w]
+
+    for pattern in ("rggb", "gbrg"):
+        out = lutc.demosaic(torch.from_numpy(img).cuda(), pattern, bits, A=shifted(A), G=shifted(G), O=shifted(O))
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy(), _ref(img, w, pattern, bits, (A, G, O)))
 
 
 def test_paper_frame_2048_16bit():
