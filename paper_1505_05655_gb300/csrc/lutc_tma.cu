@@ -230,11 +230,13 @@ __device__ __forceinline__ void row8(const uint4 v, int n, const int32_t (&A)[8]
     }
 }
 
+// The job's descriptor stays in memory (the job table, or the kernel parameters of a single-image
+// launch); the walk keeps only the fields it needs on every tile in registers.
 template <bool kBatch, class Args>
-__device__ __forceinline__ JobDesc job_of(const Args& a, int j)
+__device__ __forceinline__ const JobDesc* job_ptr(const Args& a, int j)
 {
-    if constexpr (kBatch) return a.jobs[j];
-    else return a.job;
+    if constexpr (kBatch) return a.jobs + j;
+    else return &a.job;
 }
 
 template <bool kBatch, class Args>
@@ -245,9 +247,9 @@ __device__ __forceinline__ const CUtensorMap* map_of(const Args& a, int j)
 }
 
 template <bool kBatch, class Args>
-__device__ __forceinline__ BandCoef coef_of(const Args& a, const JobDesc& J, int band)
+__device__ __forceinline__ BandCoef coef_of(const Args& a, const JobDesc* J, int band)
 {
-    if constexpr (kBatch) return J.coef[band];
+    if constexpr (kBatch) return J->coef[band];
     else return a.coef[band];
 }
 
@@ -306,14 +308,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
         }
         j = lo;
     }
-    JobDesc J = job_of<kBatch>(a, j);
+    const JobDesc* Jp = job_ptr<kBatch>(a, j);
+    int H = Jp->H;
     int row, band, strip;
     {
-        const int64_t r = u0 - J.unit_begin;
-        const int64_t seg = r / J.H;
-        row = (int)(r - seg * J.H);
-        band = (int)(seg / J.strips);
-        strip = (int)(seg - (int64_t)band * J.strips);
+        const int64_t r = u0 - Jp->unit_begin;
+        const int64_t seg = r / H;
+        row = (int)(r - seg * H);
+        const int strips = Jp->strips;
+        band = (int)(seg / strips);
+        strip = (int)(seg - (int64_t)band * strips);
     }
     int stage = 0;
     uint32_t phase = 0;
@@ -324,31 +328,34 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
         int issued = 0;
         bool ok = true;
         if constexpr (kBatch) tma_prefetch_map(map_of<kBatch>(a, j));
+        int W = Jp->W;
         while (left > 0) {
-            const int nrows = (int)min((int64_t)min(RT, J.H - row), left);
+            const int nrows = (int)min((int64_t)min(RT, H - row), left);
             if (issued >= kStages && !mbar_wait(&empty[stage], phase ^ 1u)) {
                 ok = false;
                 break;
             }
             const int x0 = strip * SW;
-            const int nb = min(NB, (J.W - x0 + 255) >> 8);
+            const int nb = min(NB, (W - x0 + 255) >> 8);
             mbar_arrive_expect_tx(&full[stage], (uint32_t)(nb * 512 * RT));
             unsigned char* dst = ring + stage * kTileBytes;
-            const int y = band * J.H + row;
+            const int y = band * H + row;
             const CUtensorMap* map = map_of<kBatch>(a, j);
             for (int b = 0; b < nb; ++b) tma_load_2d(dst + b * (RT * 512), map, &full[stage], x0 + b * 256, y);
             ++issued;
             left -= nrows;
             row += nrows;
-            if (row == J.H) {
+            if (row == H) {
                 row = 0;
-                if (++strip == J.strips) {
+                if (++strip == Jp->strips) {
                     strip = 0;
-                    if (++band == J.bands) {
+                    if (++band == Jp->bands) {
                         band = 0;
                         if (kBatch && left > 0) {
-                            J = job_of<kBatch>(a, ++j);
+                            Jp = job_ptr<kBatch>(a, ++j);
                             tma_prefetch_map(map_of<kBatch>(a, j));
+                            H = Jp->H;
+                            W = Jp->W;
                         }
                     }
                 }
@@ -373,7 +380,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
     uint32_t sync_phase = 0;
     bool new_seg = true;
     bool have_band = false;
-    int L = 1 << J.bits;
+    int L = 1 << Jp->bits;
     int32_t M = L - 1;
     uint32_t M2 = (uint32_t)M | ((uint32_t)M << 16);
     unsigned long long* hb = nullptr;  // global histogram of the band being counted
@@ -382,8 +389,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
     bool fits = true;
     bool masked = false;  // this warp holds the right-edge partial chunk of its strip
     int n = 0, c0 = 0;
+    constexpr int64_t esize = MODE == kApplyDetector ? 2 : 1;  // output bytes per pixel
+    uint8_t* orow = nullptr;  // output passes: this thread's first byte of row (row + ph) of the segment
+    int64_t opitch = 0;
+    int vout = 0;
     while (left > 0) {
-        const int nrows = (int)min((int64_t)min(RT, J.H - row), left);
+        const int nrows = (int)min((int64_t)min(RT, H - row), left);
         if (new_seg) {
             if (strip == 0 || !have_band) {
                 // a new band (of this or the next job) starts
@@ -399,14 +410,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
                     }
                     if (!consumer_sync(csync, sync_phase)) return;
                 }
-                L = 1 << J.bits;
+                L = 1 << Jp->bits;
                 M = L - 1;
                 M2 = (uint32_t)M | ((uint32_t)M << 16);
-                hb = a.hist + J.hist_off + (int64_t)band * L;
+                hb = a.hist + Jp->hist_off + (int64_t)band * L;
                 hb_len = L;
                 if (MODE == kApplyStretch) {
                     if (have_band && !consumer_sync(csync, sync_phase)) return;
-                    const uint4* src = reinterpret_cast<const uint4*>(a.S + J.S_off + (int64_t)band * L);
+                    const uint4* src = reinterpret_cast<const uint4*>(a.S + Jp->S_off + (int64_t)band * L);
                     for (int i = tid; i < L / 16; i += kConsumers) reinterpret_cast<uint4*>(table)[i] = src[i];
                     if (!consumer_sync(csync, sync_phase)) return;
                 }
@@ -414,9 +425,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
             }
             new_seg = false;
             c0 = strip * SW + ct * 8;
-            n = min(8, J.W - c0);
+            n = min(8, Jp->W - c0);
+            if constexpr (MODE >= kApplyStretch) {
+                opitch = Jp->out_pitch;
+                vout = Jp->vout;
+                orow = Jp->out + ((int64_t)band * H + row + ph) * opitch + (int64_t)c0 * esize;
+            }
             fits = true;
-            const BandCoef cf = coef_of<kBatch>(a, J, band);
+            const BandCoef cf = coef_of<kBatch>(a, Jp, band);
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj) {
                 if (jj < n) {
@@ -439,35 +455,30 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
         }
         if (!mbar_wait(&full[stage], phase)) return;
         const unsigned char* tile = my + stage * kTileBytes;
-        const int64_t orow0 = (int64_t)band * J.H + row + ph;
         if (fits && n > 0) {
             // int32-exact columns; a right-edge chunk (n < 8) reads TMA's zero fill past the
             // edge and masks those pixels out, so it stays on this path too
-            const int64_t esize = MODE == kApplyDetector ? 2 : 1;
-            uint8_t* out0 = MODE >= kApplyStretch ? J.out + orow0 * J.out_pitch + (int64_t)c0 * esize : nullptr;
             if (!masked) {
 #pragma unroll
                 for (int i = 0; i < kRowsPerThread; ++i)
                     if (ph + i * P < nrows)
                         row8<MODE, true>(*reinterpret_cast<const uint4*>(tile + i * P * 512), 8, A, G, O, M, M2,
-                                         hs, hb, table, out0 + (MODE >= kApplyStretch ? i * P * J.out_pitch : 0),
-                                         J.vout);
+                                         hs, hb, table, orow + (MODE >= kApplyStretch ? i * P * opitch : 0), vout);
             } else {
 #pragma unroll
                 for (int i = 0; i < kRowsPerThread; ++i)
                     if (ph + i * P < nrows)
                         row8<MODE, false>(*reinterpret_cast<const uint4*>(tile + i * P * 512), n, A, G, O, M, M2,
-                                          hs, hb, table, out0 + (MODE >= kApplyStretch ? i * P * J.out_pitch : 0),
-                                          J.vout);
+                                          hs, hb, table, orow + (MODE >= kApplyStretch ? i * P * opitch : 0), vout);
             }
         } else if (n > 0) {
             // a column that needs int64: exact, slow, few registers
-            const BandCoef cf = coef_of<kBatch>(a, J, band);
+            const BandCoef cf = coef_of<kBatch>(a, Jp, band);
 #pragma unroll 1
             for (int i = 0; i < kRowsPerThread; ++i) {
                 if (ph + i * P >= nrows) break;
                 const uint16_t* px = reinterpret_cast<const uint16_t*>(tile + i * P * 512);
-                const int64_t orow = orow0 + i * P;
+                uint8_t* o = orow + (MODE >= kApplyStretch ? i * P * opitch : 0);
 #pragma unroll 1
                 for (int jj = 0; jj < n; ++jj) {
                     const uint32_t x = min((uint32_t)px[jj], (uint32_t)M);
@@ -475,8 +486,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
                         det_i64(__ldg(cf.A + c0 + jj), __ldg(cf.G + c0 + jj), __ldg(cf.O + c0 + jj), x, M);
                     if (MODE == kHist) atomicAdd(hs + d, 1u);
                     else if (MODE == kHistGlobal) atomicAdd(hb + d, 1ull);
-                    else if (MODE == kApplyStretch) J.out[orow * J.out_pitch + c0 + jj] = table[d];
-                    else reinterpret_cast<uint16_t*>(J.out + orow * J.out_pitch)[c0 + jj] = (uint16_t)d;
+                    else if (MODE == kApplyStretch) o[jj] = table[d];
+                    else reinterpret_cast<uint16_t*>(o)[jj] = (uint16_t)d;
                 }
             }
         }
@@ -484,14 +495,18 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
         if (lane == 0) mbar_arrive(&empty[stage]);
         left -= nrows;
         row += nrows;
-        if (row == J.H) {
+        if constexpr (MODE >= kApplyStretch) orow += (int64_t)nrows * opitch;
+        if (row == H) {
             row = 0;
             new_seg = true;
-            if (++strip == J.strips) {
+            if (++strip == Jp->strips) {
                 strip = 0;
-                if (++band == J.bands) {
+                if (++band == Jp->bands) {
                     band = 0;
-                    if (kBatch && left > 0) J = job_of<kBatch>(a, ++j);
+                    if (kBatch && left > 0) {
+                        Jp = job_ptr<kBatch>(a, ++j);
+                        H = Jp->H;
+                    }
                 }
             }
         }
