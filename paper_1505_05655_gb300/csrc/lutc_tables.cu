@@ -114,18 +114,44 @@ __device__ __forceinline__ unsigned long long warp_incl_scan(unsigned long long 
 }
 
 // (S) for one band's histogram h (2^bits bins): writes S (2^bits bytes) and lohi[0..1].
-// Called by all kScanThreads threads of a block.
+// Called by all kScanThreads threads of a block; PER = bins per thread (2^bits / kScanThreads, at
+// least 1), so a thread's run lies wholly inside [0, 2^bits) or wholly past it.  The run is read by
+// independent loads, CH bins at a time, kept in registers when the whole run fits (CH = PER).
+template <int PER>
 __device__ __forceinline__ void stretch_band(const unsigned long long* __restrict__ h, int bits,
                                              uint8_t* __restrict__ S, int32_t* __restrict__ lohi)
 {
+    constexpr int CH = PER < 16 ? PER : 16;
+    constexpr int NCH = PER / CH;
     __shared__ unsigned long long warp_tot[kScanThreads / 32];
     __shared__ int s_lo, s_hi;
     const int L = 1 << bits;
-    const int per = (L + kScanThreads - 1) / kScanThreads;
-    const int v0 = min(L, (int)threadIdx.x * per), v1 = min(L, v0 + per);
-
+    const int v0 = (int)threadIdx.x * PER;
+    // pairs of bins by 16-byte loads when the histogram allows it (runs start on even bins)
+    const bool vec = PER >= 2 && (reinterpret_cast<uintptr_t>(h) & 15) == 0;
+    unsigned long long c[CH];
+    auto load = [&](int v) {
+        if (v >= L) {
+#pragma unroll
+            for (int k = 0; k < CH; ++k) c[k] = 0;
+        } else if (vec) {
+#pragma unroll
+            for (int k = 0; k < CH; k += 2) {
+                const ulonglong2 w = __ldg(reinterpret_cast<const ulonglong2*>(h + v + k));
+                c[k] = w.x;
+                c[k + 1] = w.y;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < CH; ++k) c[k] = __ldg(h + v + k);
+        }
+    };
     unsigned long long run = 0;
-    for (int v = v0; v < v1; ++v) run += h[v];
+    for (int ch = 0; ch < NCH; ++ch) {
+        load(v0 + ch * CH);
+#pragma unroll
+        for (int k = 0; k < CH; ++k) run += c[k];
+    }
     // block-wide inclusive scan of the run totals
     unsigned long long inc = warp_incl_scan(run);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -144,27 +170,51 @@ __device__ __forceinline__ void stretch_band(const unsigned long long* __restric
     // first v of this run with 100 cdf(v) >= 2N (resp. 98N)
     unsigned long long cdf = before;
     int my_lo = L, my_hi = L;
-    for (int v = v0; v < v1; ++v) {
-        cdf += h[v];
-        if (my_lo == L && 100ull * cdf >= 2ull * N) my_lo = v;
-        if (my_hi == L && 100ull * cdf >= 98ull * N) { my_hi = v; break; }
+    for (int ch = 0; ch < NCH; ++ch) {
+        if (NCH > 1) load(v0 + ch * CH);  // a single chunk is still in c
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+            cdf += c[k];
+            if (my_lo == L && 100ull * cdf >= 2ull * N) my_lo = v0 + ch * CH + k;
+            if (my_hi == L && 100ull * cdf >= 98ull * N) my_hi = v0 + ch * CH + k;
+        }
     }
-    if (my_lo < L) atomicMin(&s_lo, my_lo);
-    if (my_hi < L) atomicMin(&s_hi, my_hi);
+    if (v0 < L) {
+        if (my_lo < L) atomicMin(&s_lo, my_lo);
+        if (my_hi < L) atomicMin(&s_hi, my_hi);
+    }
     __syncthreads();
     const int lo = s_lo, hi = s_hi;
     if (threadIdx.x == 0) {
         lohi[0] = lo;
         lohi[1] = hi;
     }
-    const int64_t span = (int64_t)hi - lo;
+    // S[v] = clamp(((v - lo) 255 + (hi - lo) / 2) / (hi - lo), 0, 255), C division (truncation);
+    // |v - lo| < 2^16, so the numerator fits int32 and the 32-bit quotient is the int64 one
+    const int span = hi - lo;
     for (int v = threadIdx.x; v < L; v += kScanThreads) {
-        int64_t s = 0;
+        int q = 0;
         if (span != 0) {
-            s = (((int64_t)v - lo) * 255 + span / 2) / span;
-            s = s < 0 ? 0 : (s > 255 ? 255 : s);
+            q = ((v - lo) * 255 + span / 2) / span;
+            q = q < 0 ? 0 : (q > 255 ? 255 : q);
         }
-        S[v] = (uint8_t)s;
+        S[v] = (uint8_t)q;
+    }
+}
+
+// Runs stretch_band with the run length of `bits`.
+__device__ __forceinline__ void stretch_band_bits(const unsigned long long* __restrict__ h, int bits,
+                                                  uint8_t* __restrict__ S, int32_t* __restrict__ lohi)
+{
+    static_assert(kScanThreads == 1024, "run lengths below assume 1024 threads");
+    switch (bits) {
+    case 16: stretch_band<64>(h, bits, S, lohi); break;
+    case 15: stretch_band<32>(h, bits, S, lohi); break;
+    case 14: stretch_band<16>(h, bits, S, lohi); break;
+    case 13: stretch_band<8>(h, bits, S, lohi); break;
+    case 12: stretch_band<4>(h, bits, S, lohi); break;
+    case 11: stretch_band<2>(h, bits, S, lohi); break;
+    default: stretch_band<1>(h, bits, S, lohi); break;  // 8..10 bits
     }
 }
 
@@ -173,7 +223,7 @@ __global__ void __launch_bounds__(kScanThreads) k_stretch(const unsigned long lo
 {
     const int64_t L = (int64_t)1 << bits;
     const int b = blockIdx.x;
-    stretch_band(hist + b * L, bits, S + b * L, lohi + 2 * b);
+    stretch_band_bits(hist + b * L, bits, S + b * L, lohi + 2 * b);
 }
 
 // One block per (image, band) of a batch, each with its own bit depth and table offsets.
@@ -182,7 +232,7 @@ __global__ void __launch_bounds__(kScanThreads) k_stretch_batch(const TableDesc*
                                                                 uint8_t* __restrict__ S, int32_t* __restrict__ lohi)
 {
     const TableDesc d = t[blockIdx.x];
-    stretch_band(hist + d.hist_off, d.bits, S + d.S_off, lohi + d.lohi_off);
+    stretch_band_bits(hist + d.hist_off, d.bits, S + d.S_off, lohi + d.lohi_off);
 }
 
 // ---------------------------------------------------------------------------

@@ -108,6 +108,28 @@ def test_hist_every_bit_depth(bits):
     assert int(host(hist).sum()) == 2 * 129 * 4133
 
 
+@pytest.mark.parametrize("bits", list(range(8, 17)))
+@pytest.mark.parametrize("offset", [0, 1])
+def test_stretch_every_bit_depth_and_alignment(bits, offset):
+    # offset 1: the histogram starts 8 bytes off a 16-byte boundary (bins read one by one)
+    L = 1 << bits
+    rng = np.random.default_rng(bits * 7 + offset)
+    h = np.zeros((3, L), np.uint64)
+    h[0] = rng.integers(0, 1000, L).astype(np.uint64)
+    c = L // 3  # almost all mass in five bins: lo and hi inside one thread's run
+    h[1, c:c + 5] = rng.integers(1, 10**6, 5).astype(np.uint64)
+    h[1] += rng.integers(0, 2, L).astype(np.uint64)
+    h[2] = (rng.random(L) ** 8 * 1e9).astype(np.uint64)  # long tail: thresholds far apart
+    flat = np.zeros(3 * L + 1, np.uint64)
+    flat[offset:offset + 3 * L] = h.ravel()
+    hist = dev(flat)[offset:offset + 3 * L].view(3, L)
+    S, lohi = lutc.stretch(hist, bits)
+    for b in range(3):
+        rS, lo, hi = oracle.stretch(h[b], bits)
+        np.testing.assert_array_equal(host(S[b]), rS)
+        assert tuple(host(lohi[b])) == (lo, hi)
+
+
 def test_stretch_degenerate_histograms():
     bits = 12
     L = 1 << bits
