@@ -67,6 +67,19 @@ def csrc_hash(workload: str) -> str:
     return h.hexdigest()[:16]
 
 
+def ncu_l1tex_busy(kernel: str, workload: str):
+    """L1TEX / shared-memory pipe utilisation of `kernel` from the committed ncu capture, if it was
+    taken on this source (the pipe that bounds a kernel whose DRAM fraction is low)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            e = json.load(f)[workload][kernel]
+        if e.get("csrc") != csrc_hash(workload) or "l1tex_busy" not in e:
+            return None
+        return {"busy": float(e["l1tex_busy"]), "source": e.get("l1tex_capture"), "kind": "ncu, cold launch"}
+    except Exception:
+        return None
+
+
 def ncu_traffic(kernel: str, workload: str, units: float | None = None):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on this source.
 
@@ -343,6 +356,7 @@ def run_lutc(args, wl):
         ach = alg[dom] / (avg[dom] * 1e-3) / 1e9
         line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                             "traffic": ncu_traffic(names[dom].split()[0], wl.name), "kernel": names[dom],
+                            "l1tex": ncu_l1tex_busy(names[dom].split()[0], wl.name),
                             "peak_source": peak_src + " (copy bandwidth)",
                             "alg_bytes_per_launch": alg[dom]}
         line["phases_ms"] = {"pass1_hist": avg[0], "scan": avg[1], "pass2_apply": avg[2],
