@@ -460,6 +460,18 @@ LUTC_API int lutc_batch_tables(lutc_batch batch, int job, uint64_t** hist, uint8
 LUTC_API int lutc_batch_destroy(lutc_batch batch);
 
 /**
+ * The whole batch in one call: plans the jobs as lutc_batch_create does,
+ * enqueues them once on `stream` (no graph) and releases the plan.  config
+ * may be NULL (automatic configuration); a configuration returned by
+ * lutc_batch_autotune for the same kind of batch may be passed instead (its
+ * use_graph is ignored).  workspace: lutc_batch_workspace(jobs, n) bytes of
+ * device memory, 256-byte aligned, in use until the enqueued work completes.
+ * Returns what lutc_batch_create or lutc_batch_run returns.
+ */
+LUTC_API int lutc_batch_correct(const lutc_job* jobs, int n, const lutc_batch_config* config, void* workspace,
+                                size_t workspace_bytes, lutc_stream stream);
+
+/**
  * The batch autotuner: times every launch configuration (strip width x
  * blocks per SM) on these jobs -- `reps` runs each after one warm-up run, CUDA
  * events on `stream`, which it synchronises -- and writes the fastest to

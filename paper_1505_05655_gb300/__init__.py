@@ -255,25 +255,10 @@ class Batch:
 
     def __init__(self, images, column_threads: int = 0, blocks_per_sm: int = 0, use_graph: bool = True,
                  stream=None, config=None):
-        from ._lib import BatchConfig, Job
-        self._keep = []
-        n = len(images)
-        self.jobs = (Job * max(1, n))()
-        dev = None
-        for i, (raw, A, G, O, bits, out, stretch) in enumerate(images):
-            desc = raster_desc(raw, bits)
-            cd = coeff_descs(A, G, O)
-            out_t, pitch = _out_like(raw, torch.uint8 if stretch else torch.uint16, out)
-            self._keep.append((cd, raw, A, G, O, out_t))
-            self.jobs[i] = Job(desc, ctypes.cast(cd, ctypes.POINTER(Coeffs)), out_t.data_ptr(), pitch,
-                               LUTC_STRETCH if stretch else 0)
-            dev = raw.device
-        self.n = n
-        self.device = dev if dev is not None else torch.device("cuda")
-        need = int(lib().lutc_batch_workspace(self.jobs, n))
-        if need == 0 and n > 0:
-            raise LutcError(-1, "lutc_batch_workspace")
-        self.workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
+        from ._lib import BatchConfig
+        self.jobs, self._keep, self.device = _batch_jobs(images)
+        n = self.n = len(images)
+        self.workspace = _batch_workspace(self.jobs, n, self.device)
         if config is None:
             config = BatchConfig(column_threads, blocks_per_sm, 1 if use_graph else 0)
         self.config = config
@@ -312,6 +297,43 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _batch_jobs(images):
+    """(lutc_job array, the objects it points into, device) for ``(raw, A, G, O, bits, out, stretch)`` tuples."""
+    from ._lib import Job
+    keep = []
+    jobs = (Job * max(1, len(images)))()
+    dev = None
+    for i, (raw, A, G, O, bits, out, stretch) in enumerate(images):
+        desc = raster_desc(raw, bits)
+        cd = coeff_descs(A, G, O)
+        out_t, pitch = _out_like(raw, torch.uint8 if stretch else torch.uint16, out)
+        keep.append((cd, raw, A, G, O, out_t))
+        jobs[i] = Job(desc, ctypes.cast(cd, ctypes.POINTER(Coeffs)), out_t.data_ptr(), pitch,
+                      LUTC_STRETCH if stretch else 0)
+        dev = raw.device
+    return jobs, keep, dev if dev is not None else torch.device("cuda")
+
+
+def _batch_workspace(jobs, n: int, device) -> torch.Tensor:
+    need = int(lib().lutc_batch_workspace(jobs, n))
+    if need == 0 and n > 0:
+        raise LutcError(-1, "lutc_batch_workspace")
+    return torch.empty(max(need, 256), dtype=torch.uint8, device=device)
+
+
+def batch_correct(images, config=None, workspace: torch.Tensor | None = None, stream=None):
+    """The whole batch in one call (``lutc_batch_correct``); returns the outputs.  ``images`` as for
+    :class:`Batch`; ``config`` a ``BatchConfig`` (for instance from :func:`batch_autotune`) or None."""
+    jobs, keep, dev = _batch_jobs(images)
+    n = len(images)
+    if workspace is None:
+        workspace = _batch_workspace(jobs, n, dev)
+    check(lib().lutc_batch_correct(jobs, n, ctypes.byref(config) if config is not None else None,
+                                   workspace.data_ptr(), workspace.numel(), _stream(stream, dev)),
+          "lutc_batch_correct")
+    return [k[5] for k in keep]
 
 
 def batch_autotune(images, reps: int = 3, stream=None):

@@ -125,6 +125,7 @@ SIGNATURES = {
     "lutc_batch_run": (_I, [_P, _P]),
     "lutc_batch_tables": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "lutc_batch_destroy": (_I, [_P]),
+    "lutc_batch_correct": (_I, [ctypes.POINTER(Job), _I, ctypes.POINTER(BatchConfig), _P, _SZ, _P]),
     "lutc_batch_autotune": (_I, [ctypes.POINTER(Job), _I, _P, _SZ, _P, _I, ctypes.POINTER(BatchConfig),
                                  ctypes.POINTER(ctypes.c_float)]),
     "lutc_get_tuning": (_I, [_I, ctypes.POINTER(Tuning)]),

@@ -455,6 +455,19 @@ extern "C" int lutc_batch_run(lutc_batch b, lutc_stream stream)
     return cuda_status(cudaGraphLaunch(b->exec, st));
 }
 
+extern "C" int lutc_batch_correct(const lutc_job* jobs, int n, const lutc_batch_config* config, void* workspace,
+                                  size_t workspace_bytes, lutc_stream stream)
+{
+    lutc_batch_config c = config ? *config : lutc_batch_config{0, 0, 0};
+    c.use_graph = 0;  // one run: a graph would only add its capture
+    lutc_batch b = nullptr;
+    int rc = lutc_batch_create(jobs, n, &c, workspace, workspace_bytes, stream, &b);
+    if (rc) return rc;
+    rc = lutc_batch_run(b, stream);
+    lutc_batch_destroy(b);  // host state only: the enqueued work keeps nothing of it
+    return rc;
+}
+
 extern "C" int lutc_batch_tables(lutc_batch b, int job, uint64_t** hist, uint8_t** S, int32_t** lohi)
 {
     if (!b || job < 0 || job >= (int)b->jobs.size()) return LUTC_EINVAL;

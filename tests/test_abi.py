@@ -263,3 +263,13 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(got[name]) == ctypes.sizeof(py), name
         for f, _ in py._fields_:
             assert int(got["%s.%s" % (name, f)]) == getattr(py, f).offset, (name, f)
+
+
+def test_batch_correct_rejects_bad_jobs_before_launch():
+    lib = _lib.lib()
+    E = _lib.LUTC_EINVAL
+    assert lib.lutc_batch_correct(None, 1, None, None, 0, None) == E
+    assert lib.lutc_batch_correct(None, -1, None, None, 0, None) == E
+    jobs = (_lib.Job * 1)()
+    jobs[0] = _lib.Job(Raster(0x100000, 2048, 1024, 16, 1, 20), None, 0x200000, 1024, 1)  # 20-bit DN
+    assert lib.lutc_batch_correct(jobs, 1, None, ctypes.c_void_p(0x300000), 1 << 20, None) == E

@@ -5,7 +5,7 @@ that image alone, which must equal the oracle: integer arithmetic, tolerance
 zero.  The mixes below cover images the persistent TMA kernels take (aligned
 rows, width >= 256, up to 15 bits) and images they hand to the one-by-one
 path (unaligned rows, narrow, 16-bit, empty), stretch and detector-only
-images, graph capture and replay, and the autotuner.
+images, graph capture and replay, the autotuner and the one-shot call.
 """
 import numpy as np
 import pytest
@@ -92,6 +92,20 @@ def test_autotuner_picks_a_valid_configuration():
     for i, im in enumerate(ims):
         np.testing.assert_array_equal(batch.outputs()[i].cpu().numpy(), _oracle(im)[0])
     batch.close()
+
+
+@pytest.mark.parametrize("tuned", [False, True])
+def test_one_shot_batch_correct(tuned):
+    # lutc_batch_correct: plan, one run, release; with the automatic and with an autotuned configuration
+    ims = [_image(500 + i, b, h, w, bits, pad, st) for i, (b, h, w, bits, pad, st) in enumerate(MIX)]
+    dev = [_device(im) for im in ims]
+    cfg = lutc.batch_autotune(dev, reps=1)[0] if tuned else None
+    for t in (d[5] for d in dev):
+        t.view(torch.uint8).fill_(0xA5)
+    outs = lutc.batch_correct(dev, config=cfg)
+    torch.cuda.synchronize()
+    for i, im in enumerate(ims):
+        np.testing.assert_array_equal(outs[i].cpu().numpy(), _oracle(im)[0], err_msg="image %d" % i)
 
 
 def test_full_batch_workload_equals_per_image_calls():
