@@ -67,7 +67,8 @@ enum {
     LUTC_ECUDA = -4,        /**< a CUDA call or kernel launch failed */
     LUTC_ETIMEOUT = -5,     /**< a bounded wait expired */
     LUTC_EBUSY = -6,        /**< admission refused (resource budget) */
-    LUTC_ESHUTDOWN = -7     /**< the object is shutting down */
+    LUTC_ESHUTDOWN = -7,    /**< the object is shutting down */
+    LUTC_ECANCELED = -8     /**< a queued request was withdrawn (lutc_server_cancel) */
 };
 
 #define LUTC_MIN_BITS 8
@@ -554,6 +555,15 @@ LUTC_API int lutc_server_submit(lutc_server server, int sensor_id, const uint16_
  * running; the ticket stays valid) or LUTC_EINVAL (unknown ticket).
  */
 LUTC_API int lutc_server_wait(lutc_server server, uint64_t ticket, int64_t timeout_us, lutc_request_info* info);
+
+/**
+ * Withdraws a request that is still queued (not yet taken into a batch): it
+ * completes at once with status LUTC_ECANCELED and its buffers are not touched
+ * again; lutc_server_wait returns it as usual.  Returns LUTC_OK, LUTC_EBUSY when
+ * the request is already in a batch or done (it then completes normally), or
+ * LUTC_EINVAL for an unknown ticket.
+ */
+LUTC_API int lutc_server_cancel(lutc_server server, uint64_t ticket);
 
 /** Counters: requests completed, batches launched, bytes of the budget in use now, largest batch. */
 LUTC_API int lutc_server_stats(lutc_server server, uint64_t* completed, uint64_t* batches, size_t* budget_in_use,

@@ -427,6 +427,16 @@ class Server:
         self._keep.pop(ticket, None)
         return info
 
+    def cancel(self, ticket: int) -> bool:
+        """Withdraws a queued request (it completes with LUTC_ECANCELED); False if it is already in a
+        batch or done (it then completes normally)."""
+        from ._lib import LUTC_EBUSY
+        rc = lib().lutc_server_cancel(self._h, ticket)
+        if rc == LUTC_EBUSY:
+            return False
+        check(rc, "lutc_server_cancel")
+        return True
+
     def stats(self):
         c, b, u, m = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_size_t(), ctypes.c_int32()
         check(lib().lutc_server_stats(self._h, ctypes.byref(c), ctypes.byref(b), ctypes.byref(u), ctypes.byref(m)),

@@ -20,6 +20,7 @@ LUTC_ECUDA = -4
 LUTC_ETIMEOUT = -5
 LUTC_EBUSY = -6
 LUTC_ESHUTDOWN = -7
+LUTC_ECANCELED = -8
 LUTC_STRETCH = 1
 LUTC_MAX_BANDS = 64
 LUTC_TRACE_PHASES = 3
@@ -120,6 +121,7 @@ SIGNATURES = {
     "lutc_server_stats": (_I, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                ctypes.POINTER(_SZ), ctypes.POINTER(ctypes.c_int32)]),
     "lutc_server_destroy": (_I, [_P]),
+    "lutc_server_cancel": (_I, [_P, ctypes.c_uint64]),
     "lutc_batch_create": (_I, [ctypes.POINTER(Job), _I, ctypes.POINTER(BatchConfig), _P, _SZ, _P,
                                ctypes.POINTER(_P)]),
     "lutc_batch_run": (_I, [_P, _P]),

@@ -95,6 +95,7 @@ extern "C" const char* lutc_strerror(int status)
     case LUTC_ETIMEOUT: return "timed out";
     case LUTC_EBUSY: return "admission refused";
     case LUTC_ESHUTDOWN: return "shutting down";
+    case LUTC_ECANCELED: return "cancelled";
     default: return "unknown status";
     }
 }

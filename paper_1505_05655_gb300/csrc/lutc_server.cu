@@ -341,6 +341,7 @@ void lutc_server_st::run_batcher()
             return false;
         });
         if (stop) return;
+        if (pending.empty()) continue;  // every queued request was withdrawn meanwhile
         // admission: take requests in arrival order while their memory fits
         Flight* f = new Flight();
         std::vector<int> uploads;  // sensors first used by this batch
@@ -622,6 +623,25 @@ extern "C" int lutc_server_wait(lutc_server s, uint64_t ticket, int64_t timeout_
     }
     s->tickets.erase(it);
     delete r;
+    return LUTC_OK;
+}
+
+extern "C" int lutc_server_cancel(lutc_server s, uint64_t ticket)
+{
+    if (!s) return LUTC_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) return LUTC_EINVAL;
+    Request* r = it->second;
+    // queued requests hold no reservation: admission reserves and dequeues under this lock
+    auto q = std::find(s->pending.begin(), s->pending.end(), r);
+    if (q == s->pending.end()) return LUTC_EBUSY;
+    s->pending.erase(q);
+    r->status = LUTC_ECANCELED;
+    r->t_done = now_s();
+    r->done = true;
+    s->cv_wait.notify_all();
+    s->cv_batcher.notify_all();
     return LUTC_OK;
 }
 

@@ -14,6 +14,7 @@ import synth
 pytestmark = pytest.mark.gpu
 
 import paper_1505_05655_gb300 as lutc  # noqa: E402
+from paper_1505_05655_gb300 import _lib  # noqa: E402
 
 SENSORS = [(0, 700, 1, 12), (1, 1500, 3, 10), (2, 517, 4, 14), (3, 2100, 1, 12), (4, 999, 3, 12)]
 
@@ -107,3 +108,13 @@ def test_small_budget_admits_in_turn_and_stays_exact():
         np.testing.assert_array_equal(out, _expected(pool[sid], 200))
     assert server.stats()["completed"] == 30
     server.close()
+
+
+def test_device_budget_that_cannot_be_allocated_is_refused():
+    # a petabyte budget: the server's one device allocation fails, creation reports LUTC_ENOMEM and
+    # the device stays usable
+    with pytest.raises(lutc.LutcError) as e:
+        lutc.Server(budget_bytes=1 << 50)
+    assert e.value.status == _lib.LUTC_ENOMEM
+    x = torch.ones(1024, device="cuda")
+    assert float(x.sum()) == 1024.0

@@ -96,6 +96,41 @@ def test_server_config_is_checked():
         lutc.Server(fake_device=True, streams=65)
 
 
+def test_queued_requests_can_be_withdrawn():
+    # one stream, one request per batch, 200 ms per batch: the first request runs, the rest queue
+    s = _server(max_batch=1, max_wait_us=1, streams=1, fake_latency_us=200000)
+    first = s.submit(0, *_bufs(4))
+    time.sleep(0.02)
+    queued = [s.submit(k % 4, *_bufs(4)) for k in range(5)]
+    assert s.cancel(first) is False  # already in a batch: runs to completion
+    t0 = time.perf_counter()
+    assert all(s.cancel(t) for t in queued[1::2])
+    for t in queued[1::2]:
+        info = s.wait(t)
+        assert info.status == _lib.LUTC_ECANCELED and info.batch_size == 0
+    assert time.perf_counter() - t0 < 0.15  # completed at once, not after the running batch
+    assert s.wait(first).status == 0
+    for t in queued[0::2]:
+        assert s.wait(t).status == 0
+    with pytest.raises(lutc.LutcError):
+        s.cancel(first)  # forgotten after its wait
+    assert s.stats()["completed"] == 4
+    s.close()
+
+
+def test_withdrawing_every_queued_request_leaves_the_loop_working():
+    # requests held in a long window on an idle device, all withdrawn while the batcher waits
+    s = _server(max_batch=32, max_wait_us=300000, fake_latency_us=1000, hold_when_idle=True)
+    ts = [s.submit(k % 4, *_bufs(4)) for k in range(3)]
+    assert all(s.cancel(t) for t in ts)
+    assert all(s.wait(t).status == _lib.LUTC_ECANCELED for t in ts)
+    time.sleep(0.35)  # past the window the batcher had armed for the first of them
+    info = s.wait(s.submit(1, *_bufs(4)))
+    assert info.status == 0 and info.batch_size == 1
+    assert s.stats()["batches"] == 1
+    s.close()
+
+
 def test_first_request_of_a_sensor_is_the_cache_miss():
     s = _server(max_batch=1, max_wait_us=1, fake_latency_us=100)
     infos = [s.wait(s.submit(2, *_bufs(4))) for _ in range(3)]
