@@ -73,7 +73,7 @@ def ncu_l1tex_busy(kernel: str, workload: str):
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             e = json.load(f)[workload][kernel]
-        if e.get("csrc") != csrc_hash(workload) or "l1tex_busy" not in e:
+        if e.get("l1tex_csrc", e.get("csrc")) != csrc_hash(workload) or "l1tex_busy" not in e:
             return None
         return {"busy": float(e["l1tex_busy"]), "source": e.get("l1tex_capture"), "kind": "ncu, cold launch"}
     except Exception:

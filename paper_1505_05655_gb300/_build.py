@@ -3,6 +3,12 @@
 Each ``csrc/*.cu`` translation unit is compiled in parallel with nvcc
 (``-gencode arch=compute_103a,code=sm_103a``), then linked into
 ``paper_1505_05655_gb300/_build/liblutc.so``.  No GPU is needed to build.
+
+``build(checked=True)`` makes the debug variant in ``_build/checked/``: the same
+sources with ``-DLUTC_CHECKED``, whose TMA-fed kernels check their shared-memory,
+table and output indexes and record ``LUTC_EINVAL`` in the device status word
+instead of making an access out of range.  ``LUTC_CHECKED=1`` in the environment
+makes the binding load it.
 """
 from __future__ import annotations
 
@@ -16,6 +22,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "liblutc.so")
+CHECKED_DIR = os.path.join(OUT_DIR, "checked")
+CHECKED_LIB = os.path.join(CHECKED_DIR, "liblutc.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
@@ -37,24 +45,26 @@ def _inputs() -> list[str]:
     return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    """Build ``liblutc.so`` if a source is newer than it (or ``force``); returns its path."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, checked: bool = False) -> str:
+    """Build ``liblutc.so`` (or, with ``checked``, its bounds-checking variant) if a source is newer
+    than it (or ``force``); returns its path."""
+    out_dir, lib_path = (CHECKED_DIR, CHECKED_LIB) if checked else (OUT_DIR, LIB)
+    if not force and up_to_date(lib_path):
+        return lib_path
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
-    extra = list(extra or [])
+    extra = list(extra or []) + (["-DLUTC_CHECKED"] if checked else [])
     procs = []
     objs = []
     for src in sources():
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-I", INCLUDE, "-c", src, "-o", obj]
         if verbose:
@@ -71,15 +81,15 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
             failed.append(src)
     if failed:
         raise RuntimeError("nvcc failed on: " + ", ".join(os.path.basename(f) for f in failed))
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = lib_path + ".%d.tmp" % os.getpid()
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
     if verbose:
         print(" ".join(cmd))
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -137,11 +137,20 @@ SIGNATURES = {
 _lib = None
 
 
+def checked() -> bool:
+    """True when ``LUTC_CHECKED=1`` selects the bounds-checking build of the library."""
+    return os.environ.get("LUTC_CHECKED") == "1"
+
+
 def lib(build_if_stale: bool = True) -> ctypes.CDLL:
-    """The loaded ``liblutc.so`` (built first if it is missing or older than its sources)."""
+    """The loaded ``liblutc.so`` (built first if it is missing or older than its sources), or its
+    bounds-checking variant under ``LUTC_CHECKED=1``."""
     global _lib
     if _lib is None:
-        path = _build.build() if build_if_stale else _build.LIB
+        if checked():
+            path = _build.build(checked=True) if build_if_stale else _build.CHECKED_LIB
+        else:
+            path = _build.build() if build_if_stale else _build.LIB
         if not os.path.exists(path):
             raise ImportError("lutc CUDA library not built: %s" % path)
         handle = ctypes.CDLL(path)

@@ -348,6 +348,8 @@ __global__ void __launch_bounds__(kQThreads, 3) k_demosaic_tma(const __grid_cons
         const int x0 = cur.tx * kQW, y0 = cur.ty * kQH;
         const bool ok = ptx::mbar_wait_bounded(&full[s], (uint32_t)((k / kQStages) & 1), a.status);
         if (!__syncthreads_and(ok)) break;  // the same decision in every thread
+        // (checked builds) the tile's origin lies in the frame; uniform, so every thread leaves together
+        if (!in_bounds(x0 >= 0 && x0 < a.W && y0 >= 0 && y0 < a.H && cur.tx < a.strips, a.status)) break;
         uint16_t (*st)[kQSW] = reinterpret_cast<uint16_t (*)[kQSW]>(ring[s]);
         if (kCorrect) {
             if (lane < kQLanes) {

@@ -52,6 +52,19 @@ __device__ __forceinline__ uint32_t det_i64(int32_t A, int32_t G, int32_t O, uin
     return (uint32_t)(s < 0 ? 0 : (s > M ? M : s));
 }
 
+// Debug builds (-DLUTC_CHECKED): in_bounds(ok, status) records LUTC_EINVAL in *status when a check
+// fails (the first error wins) and returns ok, so that the guarded access is skipped; release builds
+// compile every check away.
+#ifdef LUTC_CHECKED
+__device__ __forceinline__ bool in_bounds(bool ok, int* status)
+{
+    if (!ok) atomicCAS(status, 0, (int)LUTC_EINVAL);
+    return ok;
+}
+#else
+__device__ __forceinline__ bool in_bounds(bool, int*) { return true; }
+#endif
+
 // ---------------------------------------------------------------------------
 // Host-side helpers shared by the entry points.
 // ---------------------------------------------------------------------------

@@ -193,15 +193,15 @@ __device__ __forceinline__ void row8(const uint4 v, int n, const int32_t (&A)[8]
     if (MODE == kModeHist) {
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj)
-            if (kFull || jj < n) atomicAdd(hs + d[jj], 1u);
+            if ((kFull || jj < n) && in_bounds(d[jj] <= (uint32_t)M, &g_device_status)) atomicAdd(hs + d[jj], 1u);
     } else if (MODE == kModeHistGlobal) {
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj)
-            if (kFull || jj < n) atomicAdd(hb + d[jj], 1ull);
+            if ((kFull || jj < n) && in_bounds(d[jj] <= (uint32_t)M, &g_device_status)) atomicAdd(hb + d[jj], 1ull);
     } else if (MODE == kModeApplyStretch) {
         uint32_t o[8];
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) o[jj] = table[d[jj]];
+        for (int jj = 0; jj < 8; ++jj) o[jj] = in_bounds(d[jj] <= (uint32_t)M, &g_device_status) ? table[d[jj]] : 0u;
         if (kFull) {
             const uint32_t lo = o[0] | (o[1] << 8) | (o[2] << 16) | (o[3] << 24);
             const uint32_t hi = o[4] | (o[5] << 8) | (o[6] << 16) | (o[7] << 24);
@@ -411,6 +411,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
                     if (!consumer_sync(csync, sync_phase)) return;
                 }
                 L = 1 << Jp->bits;
+                if (!in_bounds(Jp->bits <= a.max_bits && band < Jp->bands, &g_device_status)) return;
                 M = L - 1;
                 M2 = (uint32_t)M | ((uint32_t)M << 16);
                 hb = a.hist + Jp->hist_off + (int64_t)band * L;
@@ -455,6 +456,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
         }
         if (!mbar_wait(&full[stage], phase)) return;
         const unsigned char* tile = my + stage * kTileBytes;
+        const bool in_range =
+            in_bounds(tile >= ring && tile + (kRowsPerThread - 1) * P * 512 + 16 <= ring + kRingBytes &&
+                          row >= 0 && nrows >= 1 && row + nrows <= H && strip < Jp->strips &&
+                          (n <= 0 || c0 + n <= Jp->W),
+                      &g_device_status);
+        if (!in_range) n = 0;  // (checked builds) the tile is skipped
         if (fits && n > 0) {
             // int32-exact columns; a right-edge chunk (n < 8) reads TMA's zero fill past the
             // edge and masks those pixels out, so it stays on this path too
@@ -484,6 +491,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
                     const uint32_t x = min((uint32_t)px[jj], (uint32_t)M);
                     const uint32_t d =
                         det_i64(__ldg(cf.A + c0 + jj), __ldg(cf.G + c0 + jj), __ldg(cf.O + c0 + jj), x, M);
+                    if (!in_bounds(d <= (uint32_t)M, &g_device_status)) continue;
                     if (MODE == kHist) atomicAdd(hs + d, 1u);
                     else if (MODE == kHistGlobal) atomicAdd(hb + d, 1ull);
                     else if (MODE == kApplyStretch) o[jj] = table[d];
