@@ -716,7 +716,7 @@ def run_serve(args):
     nsens = synth.SERVE_SENSORS
     w, _, bits, bands = synth.batch_spec(synth.SERVE_SEED, nsens)
     pool_per_sensor = 4
-    server = lutc.Server(budget_bytes=40 << 30, max_batch=32, max_wait_us=2000, streams=3)
+    server = lutc.Server(budget_bytes=40 << 30, max_batch=32, max_wait_us=2000, streams=4)
     pool = []  # (sensor, raster on device, output on device, pixels)
     pool_host = []  # (sensor, raster in pinned host memory, output in pinned host memory, pixels, keep, keep)
     for sid in range(nsens):
@@ -771,13 +771,21 @@ def run_serve(args):
                     time.sleep(0.0002)  # queue full under a closed-loop burst
                 tickets[i] = t
 
-        th = threading.Thread(target=submitter)
-        th.start()
-        for i in range(n):
-            while tickets[i] is None:
-                time.sleep(0.0001)
-            infos[i] = server.wait(tickets[i])
-        th.join()
+        if closed:
+            # saturation: the whole burst queued first, then collected (a submitting thread racing the
+            # collecting one for the interpreter let the queue run dry: the load generator, not the
+            # server, then set the rate)
+            submitter()
+            for i in range(n):
+                infos[i] = server.wait(tickets[i])
+        else:
+            th = threading.Thread(target=submitter)
+            th.start()
+            for i in range(n):
+                while tickets[i] is None:
+                    time.sleep(0.0001)
+                infos[i] = server.wait(tickets[i])
+            th.join()
         lat = np.array([infos[i].done_s - (t0 + sched[i] if not closed else infos[i].submit_s) for i in range(n)])
         px = sum(src[j][3] for j in picks)
         span = max(i.done_s for i in infos) - min(i.submit_s for i in infos)
@@ -835,7 +843,7 @@ def run_serve(args):
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": "serve: %d sensors from the batch mixture, %d pool rasters each, device-resident; "
                                    "Poisson arrivals 50/200/800 req/s; budget 40 GiB; a request launches at once on "
-                                   "an idle device, else batches <= 32 requests or 2 ms, 3 streams"
+                                   "an idle device, else batches <= 32 requests or 2 ms, 4 streams"
                                    % (nsens, pool_per_sensor), "row_align_bytes": args.row_align,
                        "l2": "inputs larger than L2 (pool %.1f GB)" % (sum(p_[3] for p_ in pool) * 2 / 1e9)},
             "latency": loads, "saturation": sat, "warmup_with_cache_misses": warm, "server": st,
