@@ -35,7 +35,7 @@ import numpy as np  # noqa: E402
 
 METRIC = "Gpixel/s & % HBM peak (fused/batched vs plain); p50/p99 served latency"
 UNIT = "Gpixel/s"
-E2E_REPEATS = 5  # interleaved runs of each end-to-end variant; the median is reported
+E2E_REPEATS = 9  # interleaved runs of each end-to-end variant; the median is reported
 FALLBACK_HBM_GBS = 6800.0
 
 
