@@ -58,12 +58,22 @@ TRAFFIC_SOURCES = {
 }
 
 
+def _code_only(text: str) -> str:
+    """Source text without comments and with whitespace collapsed: what a capture depends on."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    text = re.sub(r"#[^\n]*", lambda m: m.group(0) + "\n", text)  # keep preprocessor lines apart
+    return " ".join(text.split())
+
+
 def csrc_hash(workload: str) -> str:
+    """Hash of the code (comments and layout aside) of the sources a workload's kernels are built from."""
     h = hashlib.sha256()
     for rel in TRAFFIC_SOURCES[workload.split("/")[0]]:
-        with open(os.path.join(ROOT, "paper_1505_05655_gb300", rel), "rb") as f:
+        with open(os.path.join(ROOT, "paper_1505_05655_gb300", rel), encoding="utf-8") as f:
             h.update(rel.encode())
-            h.update(f.read())
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

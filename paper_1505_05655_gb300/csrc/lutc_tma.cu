@@ -6,31 +6,35 @@
 // whose width is at least 256 columns; other rasters take the plain strip
 // kernels of lutc_correct.cu.  Both produce identical results.
 //
-// Block = 16 consumer warps + 1 producer warp, one block per SM, persistent.
+// Block = 8 consumer warps + 1 producer warp, 3 blocks per SM, persistent (one wave).
 //  * Work: the raster is cut into column strips of 8 * TC columns (TC column
-//    threads, each owning 8 adjacent detectors); the (band, strip, row)
-//    space is laid out linearly and every block takes an equal contiguous
-//    share of it, so the grid is exactly one wave and balanced to a row.
+//    threads, each owning 8 adjacent detectors); the (band, strip, row) units
+//    of a launch are laid out linearly.  A single image gives every block an
+//    equal contiguous share; a batch gives each block a contiguous run of
+//    about equal modelled cost (starts[], planned on the host), over the
+//    concatenated units of all its images.  The job descriptor stays in
+//    memory (kernel parameters or the batch's job table): the walk keeps only
+//    the fields it needs on every tile.
 //  * Producer: one thread streams tiles of (1024 / TC) rows x (8 TC) columns
-//    (16 KB) into a 6-stage shared-memory ring with 2-D tensor TMA loads
+//    (16 KB) into a 3-stage shared-memory ring with 2-D tensor TMA loads
 //    (cp.async.bulk.tensor), completion counted on a per-stage mbarrier;
-//    96 KB are in flight per SM independent of register pressure.  Columns
-//    past the image edge and rows past the raster are zero-filled by TMA and
-//    ignored by the consumers.
+//    144 KB are in flight per SM.  Columns past the image edge and rows past
+//    the raster are zero-filled by TMA and ignored by the consumers.
 //  * Consumers: each thread reads its 8 pixels of a row (one 16-byte shared
 //    load), clamps them with a packed 16x2 min, evaluates step (L) in
-//    wrap-around int32 (Horner form x (A x + G) + O + 2^15, exact when the
-//    column bound |A| M^2 + |G| M + |O + 2^15| < 2^31 holds) and then
-//      pass 1: increments a shared-memory histogram replicated R times with
-//              the copy chosen by lane (copy c holds bin v at word v R + c, so
-//              lanes of different copies never collide on an address and
-//              rarely on a bank); at each band change and at the end the
-//              copies are summed into the band's global uint64 histogram;
+//    wrap-around int32 (det_i32: Horner form, exact when the column bound
+//    |A| M^2 + |G| M + |O + 2^15| < 2^31 holds; other columns in int64) and then
+//      pass 1: increments the band's histogram in shared memory (one warp-wide
+//              atomic per pixel); at each band change and at the end it is
+//              added into the band's global uint64 histogram;
 //      pass 2: looks up S[D] in the band's stretch table in shared memory and
 //              stores 8 output bytes per row (detector-only: 16 bytes of D).
 //  * Every wait is bounded (about two seconds of clock); on expiry the block
 //    records LUTC_ETIMEOUT in the library's device status word, the producer
 //    waits (bounded) for its copies in flight, and the block returns.
+//  * Debug builds (-DLUTC_CHECKED) check every tile offset, row, column, bin
+//    and table index (in_bounds) and record LUTC_EINVAL instead of an access
+//    out of range.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <stdint.h>
