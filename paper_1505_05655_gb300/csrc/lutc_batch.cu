@@ -4,16 +4,19 @@
 // gathers such tasks -- images of uneven width, height, bit depth and band
 // count, each with its own detector coefficients -- and runs them as one
 // persistent TMA launch per phase: the launches walk the concatenation of
-// every image's (band, strip, row) space, so the load is balanced across
-// SMs to a row no matter how the image sizes mix.  Sequence per run:
+// every image's (band, strip, row) space, each block a contiguous run of
+// about equal modelled cost (a strip row costs its valid columns plus one
+// full strip's width).  Sequence per run:
 //
-//   memset(histograms) -> pass 1 (all stretch images) -> scan (one block per
-//   image band) -> pass 2 (all stretch images) -> detector-only pass (all
+//   memset(histograms) -> pass 1 (stretch images of <= 12 bits) -> pass 1
+//   (deeper ones: larger histograms, fewer blocks per SM) -> scan (one block
+//   per image band) -> pass 2 (all stretch images) -> detector-only pass (all
 //   uint16 images) -> images the TMA kernels cannot take, one by one
 //
-// optionally captured once in a CUDA graph and replayed.  All device data
-// (job table, tensor maps, coefficient pointers, tables) lives in the
-// caller's workspace: the library allocates no device memory here.
+// optionally captured once in a CUDA graph and replayed (lutc_batch_correct:
+// planned, run once and released in one call).  All device data (job table,
+// tensor maps, coefficient pointers, tables) lives in the caller's workspace:
+// the library allocates no device memory here.
 #include <cuda.h>
 #include <stdint.h>
 #include <string.h>

@@ -5,14 +5,15 @@
 // server's core, in process: no sockets, requests are function calls.
 //
 //   submit ──> pending queue ──> batcher thread ──> in-flight batches ──> completer thread ──> wait
-//               (bounded)        admission by the      (up to `streams`,     (event polling,
-//                                device budget,         each a lutc_batch     frees memory,
-//                                window of max_batch    on its own stream)    wakes waiters)
+//               (bounded;        admission by the      (up to `streams`,     (event polling,
+//                cancel takes    device budget,         each a lutc_batch     frees memory,
+//                a request out)  window of max_batch    on its own stream)    wakes waiters)
 //                                or max_wait_us
 //
-// Continuous batching: while batches run on some streams, the batcher keeps
-// admitting new requests into the next batch on a free stream as soon as the
-// window closes and memory allows.  Device memory comes from one slab of
+// Continuous batching: a request that finds no batch on the device launches at
+// once; while batches run on some streams, the batcher gathers new requests
+// into the next batch, which leaves on a free stream when it is full, when its
+// window closes or when the device goes idle, and memory allows.  Device memory comes from one slab of
 // budget_bytes allocated at creation and handed out first-fit (Arena); it
 // holds the cached sensor coefficients, host requests' staging buffers and
 // each batch's workspace.  A request waits in the queue until its memory
