@@ -106,7 +106,10 @@ struct BatchLaunch {
     int32_t max_bits;
     int64_t unit_offset;      // first unit of the launch (jobs[0].unit_begin)
     int64_t units;
-    const int64_t* starts;    // device [grid + 1]: block k walks units [starts[k], starts[k + 1])
+    const int64_t* starts;    // device [grid + 1]: block k walks units [starts[k], starts[k + 1]); with a
+                              // counter, [nchunks + 1] chunk boundaries that blocks claim at run time
+    int32_t nchunks = 0;
+    int* counter = nullptr;   // pass 1 only: chunks claimed so far, zero before the launch (or nullptr)
     int32_t grid;
     unsigned long long* hist;
     const uint8_t* S;

@@ -69,7 +69,7 @@ constexpr int kRingBytes = kStages * kTileBytes;
 // mbarriers after the ring (full and empty per stage, one consumer barrier), then the table
 constexpr int kBarRegion = ((2 * kStages + 1) * 8 + 127) / 128 * 128;
 constexpr int kTableOffset = kRingBytes + kBarRegion;
-static_assert((2 * kStages + 1) * 8 <= kBarRegion, "barrier region");
+static_assert((2 * kStages + 1) * 8 + kStages * 4 <= kBarRegion, "barrier region (barriers, per-stage chunk ids)");
 static_assert(kTableOffset % 128 == 0, "table alignment");
 
 enum Mode { kHist = kModeHist, kHistGlobal = kModeHistGlobal, kApplyStretch = kModeApplyStretch,
@@ -98,9 +98,12 @@ struct BatchArgs {
     int64_t unit_offset;  // first unit of this launch (its jobs' unit_begin are absolute)
     int64_t units;
     int64_t units_per_block;
-    const int64_t* starts;  // [gridDim.x + 1] block boundaries in units, balanced by cost
+    const int64_t* starts;  // [gridDim.x + 1] block boundaries in units, balanced by cost (claimed
+                            // launches: [nchunks + 1] chunk boundaries)
     unsigned long long* hist;
     const uint8_t* S;
+    int32_t nchunks;        // claimed launches only: chunks of the partition
+    int* counter;           // claimed launches only: chunks claimed so far (zero before the launch)
 };
 
 // ---------------------------------------------------------------------------
@@ -260,7 +263,10 @@ __device__ __forceinline__ BandCoef coef_of(const Args& a, const JobDesc* J, int
 // One persistent kernel for both passes (MODE) and both launch kinds (kBatch).
 // The launch's work is the concatenation over its jobs of (band, strip, row)
 // units; block k takes units [k q, (k + 1) q) and walks them tile by tile.
-template <int TC, int MODE, bool kBatch, class Args>
+// kClaim (batch pass 1 of the small tables only): instead of one precomputed run, a block claims
+// chunks of the partition from a.counter until none is left, so that blocks that finish early take
+// more; each ring stage carries its tile's chunk id (-1 ends the walk).
+template <int TC, int MODE, bool kBatch, class Args, bool kClaim = false>
 __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant__ Args a)
 {
     constexpr int SW = 8 * TC;                 // strip width (columns)
@@ -293,7 +299,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
 
     // This block's share of the units, walked without divisions after the first.
     int64_t u0, u1;
-    if constexpr (kBatch) {
+    if constexpr (kClaim) {
+        u0 = 0;  // the chunks are claimed below
+        u1 = 1;
+    } else if constexpr (kBatch) {
         u0 = a.starts[blockIdx.x];
         u1 = a.starts[blockIdx.x + 1];
     } else {
@@ -301,28 +310,31 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
         u1 = min(a.units, u0 + a.units_per_block);
     }
     if (u0 >= u1) return;
-    int64_t left = u1 - u0;
+    int64_t left = kClaim ? 0 : u1 - u0;
     int j = 0;
-    if constexpr (kBatch) {
-        int lo = 0, hi = a.njobs - 1;  // last job whose first unit is <= u0
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (a.jobs[mid].unit_begin <= u0) lo = mid;
-            else hi = mid - 1;
+    const JobDesc* Jp = job_ptr<kBatch>(a, 0);
+    int H = 0, row = 0, band = 0, strip = 0;
+    auto seek = [&](int64_t u) {  // the walk's position at unit u
+        if constexpr (kBatch) {
+            int lo = 0, hi = a.njobs - 1;  // last job whose first unit is <= u
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.jobs[mid].unit_begin <= u) lo = mid;
+                else hi = mid - 1;
+            }
+            j = lo;
         }
-        j = lo;
-    }
-    const JobDesc* Jp = job_ptr<kBatch>(a, j);
-    int H = Jp->H;
-    int row, band, strip;
-    {
-        const int64_t r = u0 - Jp->unit_begin;
+        Jp = job_ptr<kBatch>(a, j);
+        H = Jp->H;
+        const int64_t r = u - Jp->unit_begin;
         const int64_t seg = r / H;
         row = (int)(r - seg * H);
         const int strips = Jp->strips;
         band = (int)(seg / strips);
         strip = (int)(seg - (int64_t)band * strips);
-    }
+    };
+    if constexpr (!kClaim) seek(u0);
+    int* stage_chunk = reinterpret_cast<int*>(csync + 1);  // claimed launches: each stage's chunk id
     int stage = 0;
     uint32_t phase = 0;
 
@@ -331,40 +343,98 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
         if (tid != kConsumers) return;
         int issued = 0;
         bool ok = true;
-        if constexpr (kBatch) tma_prefetch_map(map_of<kBatch>(a, j));
-        int W = Jp->W;
-        while (left > 0) {
-            const int nrows = (int)min((int64_t)min(RT, H - row), left);
-            if (issued >= kStages && !mbar_wait(&empty[stage], phase ^ 1u)) {
-                ok = false;
-                break;
+        if constexpr (kClaim) {
+            int c = atomicAdd(a.counter, 1);
+            while (ok && c < a.nchunks) {
+                const int64_t cu0 = a.starts[c], cu1 = a.starts[c + 1];
+                if (cu0 < cu1) {
+                    seek(cu0);
+                    tma_prefetch_map(map_of<kBatch>(a, j));
+                    int W = Jp->W;
+                    left = cu1 - cu0;
+                    while (left > 0) {
+                        const int nrows = (int)min((int64_t)min(RT, H - row), left);
+                        if (issued >= kStages && !mbar_wait(&empty[stage], phase ^ 1u)) {
+                            ok = false;
+                            break;
+                        }
+                        const int x0 = strip * SW;
+                        const int nb = min(NB, (W - x0 + 255) >> 8);
+                        stage_chunk[stage] = c;  // published by the arrive below
+                        mbar_arrive_expect_tx(&full[stage], (uint32_t)(nb * 512 * RT));
+                        unsigned char* dst = ring + stage * kTileBytes;
+                        const int y = band * H + row;
+                        const CUtensorMap* map = map_of<kBatch>(a, j);
+                        for (int b = 0; b < nb; ++b)
+                            tma_load_2d(dst + b * (RT * 512), map, &full[stage], x0 + b * 256, y);
+                        ++issued;
+                        left -= nrows;
+                        row += nrows;
+                        if (row == H) {
+                            row = 0;
+                            if (++strip == Jp->strips) {
+                                strip = 0;
+                                if (++band == Jp->bands) {
+                                    band = 0;
+                                    if (left > 0) {
+                                        Jp = job_ptr<kBatch>(a, ++j);
+                                        tma_prefetch_map(map_of<kBatch>(a, j));
+                                        H = Jp->H;
+                                        W = Jp->W;
+                                    }
+                                }
+                            }
+                        }
+                        if (++stage == kStages) { stage = 0; phase ^= 1u; }
+                    }
+                }
+                if (ok) c = atomicAdd(a.counter, 1);
             }
-            const int x0 = strip * SW;
-            const int nb = min(NB, (W - x0 + 255) >> 8);
-            mbar_arrive_expect_tx(&full[stage], (uint32_t)(nb * 512 * RT));
-            unsigned char* dst = ring + stage * kTileBytes;
-            const int y = band * H + row;
-            const CUtensorMap* map = map_of<kBatch>(a, j);
-            for (int b = 0; b < nb; ++b) tma_load_2d(dst + b * (RT * 512), map, &full[stage], x0 + b * 256, y);
-            ++issued;
-            left -= nrows;
-            row += nrows;
-            if (row == H) {
-                row = 0;
-                if (++strip == Jp->strips) {
-                    strip = 0;
-                    if (++band == Jp->bands) {
-                        band = 0;
-                        if (kBatch && left > 0) {
-                            Jp = job_ptr<kBatch>(a, ++j);
-                            tma_prefetch_map(map_of<kBatch>(a, j));
-                            H = Jp->H;
-                            W = Jp->W;
+            if (ok) {
+                // the end of the walk: a stage without a copy, chunk -1
+                if (issued >= kStages && !mbar_wait(&empty[stage], phase ^ 1u)) {
+                    ok = false;
+                } else {
+                    stage_chunk[stage] = -1;
+                    mbar_arrive(&full[stage]);
+                }
+            }
+        } else {
+            if constexpr (kBatch) tma_prefetch_map(map_of<kBatch>(a, j));
+            int W = Jp->W;
+            while (left > 0) {
+                const int nrows = (int)min((int64_t)min(RT, H - row), left);
+                if (issued >= kStages && !mbar_wait(&empty[stage], phase ^ 1u)) {
+                    ok = false;
+                    break;
+                }
+                const int x0 = strip * SW;
+                const int nb = min(NB, (W - x0 + 255) >> 8);
+                mbar_arrive_expect_tx(&full[stage], (uint32_t)(nb * 512 * RT));
+                unsigned char* dst = ring + stage * kTileBytes;
+                const int y = band * H + row;
+                const CUtensorMap* map = map_of<kBatch>(a, j);
+                for (int b = 0; b < nb; ++b) tma_load_2d(dst + b * (RT * 512), map, &full[stage], x0 + b * 256, y);
+                ++issued;
+                left -= nrows;
+                row += nrows;
+                if (row == H) {
+                    row = 0;
+                    if (++strip == Jp->strips) {
+                        strip = 0;
+                        if (++band == Jp->bands) {
+                            band = 0;
+                            if (kBatch && left > 0) {
+                                Jp = job_ptr<kBatch>(a, ++j);
+                                tma_prefetch_map(map_of<kBatch>(a, j));
+                                H = Jp->H;
+                                W = Jp->W;
+                            }
                         }
                     }
                 }
+                if (++stage == kStages) { stage = 0; phase ^= 1u; }
             }
-            if (++stage == kStages) { stage = 0; phase ^= 1u; }
         }
         if (!ok) {
             // let every copy issued land before the block's shared memory goes away
@@ -397,11 +467,29 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
     uint8_t* orow = nullptr;  // output passes: this thread's first byte of row (row + ph) of the segment
     int64_t opitch = 0;
     int vout = 0;
-    while (left > 0) {
+    int cur_c = -1;    // claimed launches: the chunk being walked
+    int tab_key = -1;  // claimed launches: (job << 8) | band of the histogram held
+    for (;;) {
+        if constexpr (kClaim) {
+            if (!mbar_wait(&full[stage], phase)) return;
+            const int c = stage_chunk[stage];
+            if (c < 0) break;  // the walk is over
+            if (c != cur_c) {
+                // the first tile of another chunk: it may start anywhere, in any band
+                cur_c = c;
+                seek(a.starts[c]);
+                left = a.starts[c + 1] - a.starts[c];
+                new_seg = true;
+            }
+        } else {
+            if (left <= 0) break;
+        }
         const int nrows = (int)min((int64_t)min(RT, H - row), left);
         if (new_seg) {
-            if (strip == 0 || !have_band) {
-                // a new band (of this or the next job) starts
+            bool new_band;  // a new band (of this or another job) starts
+            if constexpr (kClaim) new_band = ((j << 8) | band) != tab_key;
+            else new_band = strip == 0 || !have_band;
+            if (new_band) {
                 if (MODE == kHist && have_band) {
                     // every consumer is done with the previous band: flush it and clear
                     if (!consumer_sync(csync, sync_phase)) return;
@@ -427,6 +515,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
                     if (!consumer_sync(csync, sync_phase)) return;
                 }
                 have_band = true;
+                if constexpr (kClaim) tab_key = (j << 8) | band;
             }
             new_seg = false;
             c0 = strip * SW + ct * 8;
@@ -458,7 +547,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
             // per tile, and the ring only advances at its slowest warp's pace.
             masked = __any_sync(0xffffffffu, n > 0 && n < 8);
         }
-        if (!mbar_wait(&full[stage], phase)) return;
+        if constexpr (!kClaim) {
+            if (!mbar_wait(&full[stage], phase)) return;
+        }
         const unsigned char* tile = my + stage * kTileBytes;
         const bool in_range =
             in_bounds(tile >= ring && tile + (kRowsPerThread - 1) * P * 512 + 16 <= ring + kRingBytes &&
@@ -661,6 +752,28 @@ int launch_batch(BatchArgs& a, int tc, int grid, cudaStream_t st)
     }
 }
 
+// Pass 1 with chunks claimed at run time (a.counter, a.nchunks).
+template <int TC>
+int launch_batch_claim_tc(BatchArgs& a, int grid, cudaStream_t st)
+{
+    auto k = k_tma_strip<TC, kHist, true, BatchArgs, true>;
+    const size_t smem = (size_t)kTableOffset + table_bytes(kHist, a.max_bits);
+    int64_t g = 0;
+    int rc = grid_for(k, smem, 0, &g);  // raises the shared-memory limit on first use
+    if (rc) return rc;
+    k<<<(unsigned)grid, kThreads, smem, st>>>(a);
+    return cuda_status(cudaGetLastError());
+}
+
+int launch_batch_claim(BatchArgs& a, int tc, int grid, cudaStream_t st)
+{
+    switch (tc) {
+    case 256: return launch_batch_claim_tc<256>(a, grid, st);
+    case 128: return launch_batch_claim_tc<128>(a, grid, st);
+    default: return launch_batch_claim_tc<64>(a, grid, st);
+    }
+}
+
 template <int MODE>
 int batch_grid(int tc, int max_bits, int blocks_per_sm)
 {
@@ -682,6 +795,7 @@ int preload_tc()
         const size_t z = (size_t)kTableOffset;
         if (!rc) rc = grid_for(k_tma_strip<TC, kHist, false, TmaArgs>, h, 0, &g);
         if (!rc) rc = grid_for(k_tma_strip<TC, kHist, true, BatchArgs>, h, 0, &g);
+        if (!rc) rc = grid_for(k_tma_strip<TC, kHist, true, BatchArgs, true>, h, 0, &g);
         if (!rc) rc = grid_for(k_tma_strip<TC, kApplyStretch, false, TmaArgs>, t, 0, &g);
         if (!rc) rc = grid_for(k_tma_strip<TC, kApplyStretch, true, BatchArgs>, t, 0, &g);
         if (!rc) rc = grid_for(k_tma_strip<TC, kApplyDetector, false, TmaArgs>, z, 0, &g);
@@ -803,6 +917,9 @@ int tma_batch_pass(const BatchLaunch& b, int mode, int column_threads, int block
     a.starts = b.starts;
     a.hist = b.hist;
     a.S = b.S;
+    a.nchunks = b.nchunks;
+    a.counter = b.counter;
+    if (mode == kHist && b.counter) return launch_batch_claim(a, column_threads, b.grid, st);
     switch (mode) {
     case kHist: return launch_batch<kHist>(a, column_threads, b.grid, st);
     case kApplyStretch: return launch_batch<kApplyStretch>(a, column_threads, b.grid, st);
