@@ -59,12 +59,17 @@ TRAFFIC_SOURCES = {
 
 
 def _code_only(text: str) -> str:
-    """Source text without comments and with whitespace collapsed: what a capture depends on."""
+    """Source text without comments and with whitespace collapsed: what a capture depends on.
+    Preprocessor lines stay lines of their own (a directive ends at its line's end)."""
     import re
     text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
     text = re.sub(r"//[^\n]*", " ", text)
-    text = re.sub(r"#[^\n]*", lambda m: m.group(0) + "\n", text)  # keep preprocessor lines apart
-    return " ".join(text.split())
+    out = []
+    for line in text.splitlines():
+        s = " ".join(line.split())
+        if s:
+            out.append("\n" + s + "\n" if s.startswith("#") else s)
+    return " ".join(out)
 
 
 def csrc_hash(workload: str) -> str:
