@@ -513,7 +513,8 @@ typedef struct {
 
 /** Per-request outcome, filled by lutc_server_wait. */
 typedef struct {
-    int32_t status;      /**< LUTC_OK, LUTC_ECUDA (failed batch), LUTC_ESHUTDOWN (server closed first) */
+    int32_t status;      /**< LUTC_OK, LUTC_ECUDA (failed batch), LUTC_ESHUTDOWN (server closed first),
+                              LUTC_ECANCELED (withdrawn by lutc_server_cancel) */
     int32_t batch_size;  /**< requests in the batch that carried it */
     double submit_s;     /**< host steady-clock seconds at submit */
     double start_s;      /**< ... when its batch was formed */
