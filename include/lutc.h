@@ -566,6 +566,36 @@ LUTC_API int lutc_server_wait(lutc_server server, uint64_t ticket, int64_t timeo
  */
 LUTC_API int lutc_server_cancel(lutc_server server, uint64_t ticket);
 
+/** One request of a replayed schedule (lutc_server_replay); the fields after at_s are lutc_server_submit's. */
+typedef struct {
+    double at_s;             /**< arrival, seconds after the replay starts (0 ..  3600, non-decreasing) */
+    const uint16_t* raster;
+    uint8_t* out;
+    int64_t pitch_bytes;
+    int64_t out_pitch_bytes;
+    int32_t sensor_id;
+    int32_t height;
+    int32_t flags;
+    int32_t pad;
+} lutc_replay_request;
+
+/**
+ * Open-loop load generator: a native thread of the library submits
+ * requests[i] when its arrival time is due (a request the queue refuses with
+ * LUTC_EBUSY is retried every 20 us, for up to 120 s), while the calling
+ * thread collects every ticket in order.  info[i] receives the request's
+ * outcome (lutc_server_wait) and scheduled_s[i] (may be NULL) the
+ * steady-clock second it was due, on the clock of info's timestamps:
+ * latency = info[i].done_s - scheduled_s[i] counts any lateness of the
+ * hand-over (info[i].submit_s - scheduled_s[i]) against the request.  All
+ * arrival times 0 make a closed burst.  Blocks until every request has
+ * completed.  Returns LUTC_OK; LUTC_EINVAL for bad arguments (nothing is
+ * submitted); or the first submit or wait error, after which the remaining
+ * requests are not submitted and their info[].status holds that error.
+ */
+LUTC_API int lutc_server_replay(lutc_server server, const lutc_replay_request* requests, int n,
+                                lutc_request_info* info, double* scheduled_s);
+
 /** Counters: requests completed, batches launched, bytes of the budget in use now, largest batch. */
 LUTC_API int lutc_server_stats(lutc_server server, uint64_t* completed, uint64_t* batches, size_t* budget_in_use,
                                int32_t* largest_batch);
@@ -603,31 +633,53 @@ LUTC_API int lutc_set_tuning(int bits, const lutc_tuning* tuning);
 /** Reads the configuration lutc_set_tuning stored for `bits` (all zero if automatic). */
 LUTC_API int lutc_get_tuning(int bits, lutc_tuning* tuning);
 
+/**
+ * Which kernel family the calling host thread's most recent call with pixels
+ * to process ran -- lutc_hist, lutc_apply_stretch or lutc_correct_image
+ * (either mode), or the host-raster calls built on them: LUTC_PATH_TMA (the
+ * TMA-staged persistent kernels) or LUTC_PATH_STRIP (the plain strip
+ * kernels); LUTC_PATH_AUTO (0) before this thread has made such a call.  The
+ * TMA family needs 16-byte aligned rows, width >= 256, bands * height < 2^31,
+ * the driver's tensor-map encoder and a tuning that allows it; a call that
+ * cannot have it runs the strip kernels with the same result, and this query
+ * is how a caller (or a measurement) sees which one ran.  Calls rejected by
+ * their argument checks, and empty rasters, leave it unchanged.  Per host
+ * thread; no GPU work.  Returns LUTC_OK, or LUTC_EINVAL when path is NULL.
+ */
+LUTC_API int lutc_last_path(int* path);
+
 /** Size of the fixed device scratch array behind lutc_correct_image_static (1 MiB per GPU). */
 #define LUTC_STATIC_SCRATCH_BYTES (1u << 20)
 
 /**
  * lutc_correct_image without a caller-provided workspace, for callers that
- * cannot allocate device memory (no device allocator of their own, an
- * allocation would stall a latency-bound loop, or their framework owns every
- * device allocation).  The paper has no counterpart: this is a convenience of
- * this library, not a step of the method.
+ * cannot allocate device memory: a plain C client with no device allocator
+ * of its own, a latency-bound loop in which an allocation would stall the
+ * device, or a framework whose memory manager owns every device allocation.
+ * The paper has no counterpart: this is a convenience of this library, not a
+ * step of the method.
  *
- * Same arguments, result and errors as lutc_correct_image, minus the
- * workspace.  The scratch (per-band histogram, stretch table and lo/hi) comes
- * from one file-scope device array of LUTC_STATIC_SCRATCH_BYTES that every GPU
- * loading the library holds until the process exits; the call allocates
- * nothing.  A raster whose tables need more than that
- * (lutc_correct_image_workspace(in) > LUTC_STATIC_SCRATCH_BYTES, e.g. 4 bands
- * at 16 bits) is rejected with LUTC_ENOMEM before anything is enqueued.
+ * Same arguments and result as lutc_correct_image, minus the workspace; the
+ * arguments are checked in the same order, so a malformed raster, a NULL
+ * coefficient set, an unknown flag or a bad output gives LUTC_EINVAL whatever
+ * the raster's size.  With LUTC_STRETCH the scratch (per-band histogram,
+ * stretch table and lo/hi) comes from one file-scope device array of
+ * LUTC_STATIC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits; the call allocates nothing.  A raster whose tables need
+ * more than that is rejected with LUTC_ENOMEM before anything is enqueued:
+ * the tables take 9 * 2^bits bytes per band (plus 256-byte rounding), so
+ * 1 MiB holds at most 1 band at 16 bits, 3 at 15, 7 at 14, 14 at 13, 28 at
+ * 12, 56 at 11 and every band count (LUTC_MAX_BANDS) at 10 bits or fewer;
+ * lutc_correct_image_workspace(in) <= LUTC_STATIC_SCRATCH_BYTES is the exact
+ * test.  Without LUTC_STRETCH no scratch is used and any raster is accepted.
  *
- * The first call on a device looks up the array's device address on the
- * current device (cudaGetSymbolAddress) and caches it; make that first call
- * before any stream capture on that device.  Every call on a device shares
- * the one array, which keeps the previous call's tables (the histogram is
- * cleared at the start of each call): calls that overlap on the GPU --
- * concurrent streams, or host threads without ordering -- race on it and give
- * wrong results.  Serialise them on one stream.
+ * The first call with LUTC_STRETCH on a device looks up the array's device
+ * address on the current device (cudaGetSymbolAddress) and caches it; make
+ * that first call before any stream capture on that device.  Every call on a
+ * device shares the one array, which keeps the previous call's tables (the
+ * histogram is cleared at the start of each call): calls that overlap on the
+ * GPU -- concurrent streams, or host threads without ordering -- race on it
+ * and give wrong results.  Serialise them on one stream.
  */
 LUTC_API int lutc_correct_image_static(const lutc_raster* in, const lutc_coeffs* per_band, int flags, void* out,
                                        int64_t out_pitch_bytes, lutc_stream stream);

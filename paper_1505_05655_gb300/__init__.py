@@ -245,6 +245,13 @@ def get_tuning(bits: int):
     return (t.path, t.column_threads, t.blocks_per_sm)
 
 
+def last_path() -> int:
+    """Kernel family (LUTC_PATH_TMA or LUTC_PATH_STRIP) of this thread's last pass-kernel call, 0 before any."""
+    p = ctypes.c_int(-1)
+    check(lib().lutc_last_path(ctypes.byref(p)), "lutc_last_path")
+    return p.value
+
+
 class Batch:
     """A prepared batch of independent corrections (``lutc_batch_*``).
 
@@ -415,6 +422,27 @@ class Server:
         if rc == 0:
             self._keep[t.value] = (raw, out, None)
         return rc, t.value
+
+    def replay(self, schedule):
+        """Open-loop replay (``lutc_server_replay``): ``schedule`` lists ``(at_s, sensor_id, raw, out, host)``
+        with non-decreasing arrival times in seconds.  A native thread submits each request when it is
+        due and this call collects them all; returns a dict of numpy arrays (``scheduled_s``,
+        ``submit_s``, ``start_s``, ``launched_s``, ``done_s``, ``batch_size``, ``status``, ``cache_miss``)."""
+        import numpy as np
+        from ._lib import LUTC_REQ_HOST, ReplayRequest, RequestInfo
+        n = len(schedule)
+        reqs = (ReplayRequest * max(1, n))()
+        for i, (at, sid, raw, out, host) in enumerate(schedule):
+            ip, pitch = self._addr_pitch(raw, 2)
+            op, opitch = self._addr_pitch(out, 1)
+            reqs[i] = ReplayRequest(float(at), ip, op, pitch, opitch, sid, raw.shape[-2], LUTC_REQ_HOST if host else 0, 0)
+        infos = (RequestInfo * max(1, n))()
+        sched = (ctypes.c_double * max(1, n))()
+        check(lib().lutc_server_replay(self._h, reqs, n, infos, sched), "lutc_server_replay")
+        res = {k: np.array([getattr(infos[i], k) for i in range(n)])
+               for k in ("submit_s", "start_s", "launched_s", "done_s", "batch_size", "status", "cache_miss")}
+        res["scheduled_s"] = np.array(sched[:n])
+        return res
 
     def wait(self, ticket: int, timeout_us: int = -1):
         """The request's RequestInfo, or None if it is still running after timeout_us."""

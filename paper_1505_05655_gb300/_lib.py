@@ -28,6 +28,7 @@ LUTC_PATH_AUTO = 0
 LUTC_PATH_TMA = 1
 LUTC_PATH_STRIP = 2
 LUTC_REQ_HOST = 2
+LUTC_STATIC_SCRATCH_BYTES = 1 << 20
 LUTC_TASK_LUTGEN, LUTC_TASK_HIST, LUTC_TASK_STRETCH, LUTC_TASK_COMPOSE = 1, 2, 3, 4
 LUTC_TASK_APPLY, LUTC_TASK_CORRECT_IMAGE, LUTC_TASK_DEVICE_INFO, LUTC_TASK_DEMOSAIC, LUTC_TASK_FIT = 5, 6, 7, 8, 9
 LUTC_BAYER = {"rggb": 0, "bggr": 1, "grbg": 2, "gbrg": 3}
@@ -58,6 +59,12 @@ class RequestInfo(ctypes.Structure):
                 ("start_s", ctypes.c_double), ("launched_s", ctypes.c_double), ("done_s", ctypes.c_double),
                 ("cache_miss", ctypes.c_int32),
                 ("pad", ctypes.c_int32)]
+
+
+class ReplayRequest(ctypes.Structure):
+    _fields_ = [("at_s", ctypes.c_double), ("raster", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("pitch_bytes", ctypes.c_int64), ("out_pitch_bytes", ctypes.c_int64), ("sensor_id", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("flags", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class Raster(ctypes.Structure):
@@ -122,6 +129,8 @@ SIGNATURES = {
                                ctypes.POINTER(_SZ), ctypes.POINTER(ctypes.c_int32)]),
     "lutc_server_destroy": (_I, [_P]),
     "lutc_server_cancel": (_I, [_P, ctypes.c_uint64]),
+    "lutc_server_replay": (_I, [_P, ctypes.POINTER(ReplayRequest), _I, ctypes.POINTER(RequestInfo),
+                                ctypes.POINTER(ctypes.c_double)]),
     "lutc_batch_create": (_I, [ctypes.POINTER(Job), _I, ctypes.POINTER(BatchConfig), _P, _SZ, _P,
                                ctypes.POINTER(_P)]),
     "lutc_batch_run": (_I, [_P, _P]),
@@ -131,6 +140,7 @@ SIGNATURES = {
     "lutc_batch_autotune": (_I, [ctypes.POINTER(Job), _I, _P, _SZ, _P, _I, ctypes.POINTER(BatchConfig),
                                  ctypes.POINTER(ctypes.c_float)]),
     "lutc_get_tuning": (_I, [_I, ctypes.POINTER(Tuning)]),
+    "lutc_last_path": (_I, [ctypes.POINTER(_I)]),
     "lutc_trace_read": (_I, [ctypes.POINTER(ctypes.c_float), _I]),
 }
 

@@ -364,7 +364,12 @@ void trace_release()
     g_trace = Trace();
 }
 
+// Kernel family of the calling host thread's last call that enqueued pass kernels (lutc_last_path).
+thread_local int t_last_path = LUTC_PATH_AUTO;
+
 }  // namespace
+
+void record_path(bool tma) { t_last_path = tma ? LUTC_PATH_TMA : LUTC_PATH_STRIP; }
 
 // events of the next traced call, or nullptr when tracing is off or full
 cudaEvent_t* trace_slot()
@@ -376,7 +381,9 @@ cudaEvent_t* trace_slot()
 int pass1_accumulate(const lutc_raster* in, const lutc_coeffs* per_band, unsigned long long* hist, cudaStream_t st)
 {
     if ((int64_t)in->width * in->height == 0) return LUTC_OK;
-    if (tma_eligible(in)) return tma_hist(in, per_band, hist, st);
+    const bool tma = tma_eligible(in);
+    record_path(tma);
+    if (tma) return tma_hist(in, per_band, hist, st);
     StripArgs a = make_args(in, per_band);
     return launch_hist(a, in, hist, st);
 }
@@ -385,7 +392,9 @@ int pass2(const lutc_raster* in, const lutc_coeffs* per_band, const uint8_t* S, 
           bool stretch, cudaStream_t st)
 {
     if ((int64_t)in->width * in->height == 0) return LUTC_OK;
-    if (tma_eligible(in)) return tma_apply(in, per_band, S, out, out_pitch, stretch, st);
+    const bool tma = tma_eligible(in);
+    record_path(tma);
+    if (tma) return tma_apply(in, per_band, S, out, out_pitch, stretch, st);
     StripArgs a = make_args(in, per_band);
     return stretch ? launch_apply<true>(a, in, S, out, out_pitch, st)
                    : launch_apply<false>(a, in, nullptr, out, out_pitch, st);
@@ -447,9 +456,18 @@ extern "C" int lutc_apply_stretch(const lutc_raster* in, const lutc_coeffs* per_
     if ((rc = check_coeff_set(in, per_band))) return rc;
     if ((int64_t)in->width * in->height == 0) return LUTC_OK;
     if (!S || ((uintptr_t)S % 16) || !out || out_pitch_bytes < in->width) return LUTC_EINVAL;
-    if (tma_eligible(in)) return tma_apply(in, per_band, S, out, out_pitch_bytes, true, (cudaStream_t)stream);
+    const bool tma = tma_eligible(in);
+    record_path(tma);
+    if (tma) return tma_apply(in, per_band, S, out, out_pitch_bytes, true, (cudaStream_t)stream);
     StripArgs a = make_args(in, per_band);
     return launch_apply<true>(a, in, S, out, out_pitch_bytes, (cudaStream_t)stream);
+}
+
+extern "C" int lutc_last_path(int* path)
+{
+    if (!path) return LUTC_EINVAL;
+    *path = t_last_path;
+    return LUTC_OK;
 }
 
 extern "C" size_t lutc_correct_image_workspace(const lutc_raster* in)
@@ -479,7 +497,9 @@ extern "C" int lutc_hist(const lutc_raster* in, const lutc_coeffs* per_band, uin
     const size_t L = (size_t)1 << in->bits;
     if ((rc = cuda_status(cudaMemsetAsync(hist, 0, (size_t)in->bands * L * 8, st)))) return rc;
     if ((int64_t)in->width * in->height == 0) return LUTC_OK;
-    if (tma_eligible(in)) return tma_hist(in, per_band, reinterpret_cast<unsigned long long*>(hist), st);
+    const bool tma = tma_eligible(in);
+    record_path(tma);
+    if (tma) return tma_hist(in, per_band, reinterpret_cast<unsigned long long*>(hist), st);
     StripArgs a = make_args(in, per_band);
     return launch_hist(a, in, reinterpret_cast<unsigned long long*>(hist), st);
 }
@@ -497,6 +517,7 @@ extern "C" int lutc_correct_image(const lutc_raster* in, const lutc_coeffs* per_
     if (!empty && (!out || out_pitch_bytes < elem * in->width || out_pitch_bytes % elem)) return LUTC_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const bool tma = !empty && tma_eligible(in);
+    if (!empty) record_path(tma);
     StripArgs a = make_args(in, per_band);
     if (!stretch) {
         if (empty) return LUTC_OK;

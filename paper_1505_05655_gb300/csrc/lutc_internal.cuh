@@ -151,6 +151,7 @@ int check_coeff_set(const lutc_raster* r, const lutc_coeffs* per_band);
 int sm_count();
 lutc_tuning tuning_for(int bits);  // the stored configuration (zeros = automatic)
 cudaEvent_t* trace_slot();         // LUTC_TRACE_PHASES + 1 events of the next traced call, or nullptr
+void record_path(bool tma);        // what lutc_last_path reports to the calling host thread
 int cuda_status(cudaError_t e);  // cudaSuccess -> LUTC_OK, else LUTC_ECUDA (and clears the sticky-free error)
 int* device_status_ptr();        // the kernel status word (lutc_device_status) of the current device, or nullptr
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();  // cuTensorMapEncodeTiled, or nullptr

@@ -53,11 +53,17 @@ int static_scratch(void** addr)
 extern "C" int lutc_correct_image_static(const lutc_raster* in, const lutc_coeffs* per_band, int flags, void* out,
                                          int64_t out_pitch_bytes, lutc_stream stream)
 {
-    const size_t need = lutc_correct_image_workspace(in);
-    if (need == 0) return LUTC_EINVAL;
-    if ((flags & LUTC_STRETCH) && need > (size_t)LUTC_STATIC_SCRATCH_BYTES) return LUTC_ENOMEM;
-    void* scratch = nullptr;
-    const int rc = static_scratch(&scratch);
+    // lutc_correct_image's own checks first, in its order, so that a malformed call gets the same
+    // LUTC_EINVAL whatever the raster's size; only then the limit of the fixed array
+    int rc = lutc::check_raster(in);
     if (rc) return rc;
+    if ((rc = lutc::check_coeff_set(in, per_band))) return rc;
+    if (flags & ~LUTC_STRETCH) return LUTC_EINVAL;
+    if (!(flags & LUTC_STRETCH))  // detector only: one pass, no scratch at all
+        return lutc_correct_image(in, per_band, flags, out, out_pitch_bytes, nullptr, 0, stream);
+    if ((int64_t)in->width * in->height > 0 && (!out || out_pitch_bytes < in->width)) return LUTC_EINVAL;
+    if (lutc_correct_image_workspace(in) > (size_t)LUTC_STATIC_SCRATCH_BYTES) return LUTC_ENOMEM;
+    void* scratch = nullptr;
+    if ((rc = static_scratch(&scratch))) return rc;
     return lutc_correct_image(in, per_band, flags, out, out_pitch_bytes, scratch, LUTC_STATIC_SCRATCH_BYTES, stream);
 }

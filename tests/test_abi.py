@@ -237,7 +237,8 @@ def test_struct_layouts_match_the_header(tmp_path):
         pytest.skip("no C compiler")
     twins = {"lutc_coeffs": _lib.Coeffs, "lutc_raster": _lib.Raster, "lutc_job": _lib.Job,
              "lutc_batch_config": _lib.BatchConfig, "lutc_server_config": _lib.ServerConfig,
-             "lutc_request_info": _lib.RequestInfo, "lutc_tuning": _lib.Tuning}
+             "lutc_request_info": _lib.RequestInfo, "lutc_tuning": _lib.Tuning,
+             "lutc_replay_request": _lib.ReplayRequest}
     text = open(HEADER).read()
     assert set(re.findall(r"^\}\s*(lutc_\w+)\s*;", text, flags=re.M)) == set(twins), "a struct has no ctypes twin"
     c_name = {"in_": "in"}
@@ -273,3 +274,57 @@ def test_batch_correct_rejects_bad_jobs_before_launch():
     jobs = (_lib.Job * 1)()
     jobs[0] = _lib.Job(Raster(0x100000, 2048, 1024, 16, 1, 20), None, 0x200000, 1024, 1)  # 20-bit DN
     assert lib.lutc_batch_correct(jobs, 1, None, ctypes.c_void_p(0x300000), 1 << 20, None) == E
+
+
+# most bands whose fused-path tables fit the 1 MiB array of lutc_correct_image_static, per bit depth
+STATIC_BAND_LIMIT = {16: 1, 15: 3, 14: 7, 13: 14, 12: 28, 11: 56, 10: 64, 9: 64, 8: 64}
+
+
+@pytest.mark.parametrize("bits", sorted(STATIC_BAND_LIMIT))
+def test_static_scratch_limit_per_bit_depth(bits):
+    # the limit the header states (9 * 2^bits bytes per band plus rounding, in 1 MiB) is exactly
+    # where the workspace query crosses the array's size
+    lib = _lib.lib()
+    fits = lambda bands: lib.lutc_correct_image_workspace(ctypes.byref(_raster(bands=bands, bits=bits))) \
+        <= _lib.LUTC_STATIC_SCRATCH_BYTES
+    n = STATIC_BAND_LIMIT[bits]
+    assert fits(n)
+    assert n == _lib.LUTC_MAX_BANDS or not fits(n + 1)
+
+
+def test_static_entry_checks_arguments_before_the_size_limit():
+    # on an oversized raster: malformed calls are LUTC_EINVAL, a well-formed one LUTC_ENOMEM; all of
+    # it on the host, before anything reaches a device
+    lib = _lib.lib()
+    r = _raster(bands=2, bits=16)
+    c = (Coeffs * 2)(*[Coeffs(0x20000, 0x30000, 0x40000, 100)] * 2)
+    out = ctypes.c_void_p(0x50000)
+    assert lib.lutc_correct_image_static(ctypes.byref(r), c, _lib.LUTC_STRETCH, out, 100, None) == _lib.LUTC_ENOMEM
+    assert lib.lutc_correct_image_static(ctypes.byref(r), c, _lib.LUTC_STRETCH | 0x100, out, 100, None) == _lib.LUTC_EINVAL
+    assert lib.lutc_correct_image_static(ctypes.byref(r), None, _lib.LUTC_STRETCH, out, 100, None) == _lib.LUTC_EINVAL
+    assert lib.lutc_correct_image_static(ctypes.byref(r), c, _lib.LUTC_STRETCH, None, 100, None) == _lib.LUTC_EINVAL
+    assert lib.lutc_correct_image_static(ctypes.byref(r), c, _lib.LUTC_STRETCH, out, 99, None) == _lib.LUTC_EINVAL
+    assert lib.lutc_correct_image_static(ctypes.byref(_raster(bits=17)), c, 0, out, 200, None) == _lib.LUTC_EINVAL
+
+
+def test_last_path_contract():
+    # per host thread: 0 before any call with pixels; calls rejected by their checks leave it alone
+    import threading
+    lib = _lib.lib()
+    seen = []
+
+    def fresh_thread():
+        p = ctypes.c_int(-1)
+        seen.append((lib.lutc_last_path(ctypes.byref(p)), p.value))
+        r = _raster()
+        good = (Coeffs * 1)(Coeffs(0x20000, 0x30000, 0x40000, 100))
+        assert lib.lutc_correct_image(ctypes.byref(r), good, 4, ctypes.c_void_p(0x50000), 100,
+                                      ctypes.c_void_p(0x60000), 1 << 20, None) == _lib.LUTC_EINVAL
+        assert lib.lutc_hist(ctypes.byref(_raster(bits=7)), good, ctypes.c_void_p(0x70000), None) == _lib.LUTC_EINVAL
+        seen.append((lib.lutc_last_path(ctypes.byref(p)), p.value))
+
+    t = threading.Thread(target=fresh_thread)
+    t.start()
+    t.join()
+    assert seen == [(0, _lib.LUTC_PATH_AUTO), (0, _lib.LUTC_PATH_AUTO)]
+    assert lib.lutc_last_path(None) == _lib.LUTC_EINVAL

@@ -234,3 +234,50 @@ def test_concurrent_submitters():
     assert len(results) == 150 and all(r == 0 for r in results)
     assert s.stats()["completed"] == 150
     s.close()
+
+
+def test_replay_keeps_its_schedule_and_collects_every_request():
+    # lutc_server_replay: requests handed over by a native thread at their scheduled times; the
+    # latency is counted from the scheduled time, so lateness of the hand-over would show
+    s = _server(max_batch=8, max_wait_us=1000, fake_latency_us=300)
+    bufs = [_bufs(8) for _ in range(16)]
+    rng = np.random.default_rng(7)
+    at = np.cumsum(rng.exponential(1 / 4000.0, 800))  # Poisson arrivals at 4000 requests per second
+    sched = [(float(t), i % 4, *bufs[i % 16], False) for i, t in enumerate(at)]
+    r = s.replay(sched)
+    assert (r["status"] == 0).all()
+    assert np.all(np.diff(r["scheduled_s"]) >= 0)
+    np.testing.assert_allclose(r["scheduled_s"] - r["scheduled_s"][0], at - at[0], atol=1e-9)
+    lag = r["submit_s"] - r["scheduled_s"]
+    assert lag.min() >= 0 and np.median(lag) < 1e-3, np.median(lag)
+    lat = r["done_s"] - r["scheduled_s"]
+    assert lat.min() >= 300e-6  # at least the fake device's latency
+    assert r["batch_size"].max() > 1  # at this rate requests share batches
+    assert s.stats()["completed"] == 800
+    s.close()
+
+
+def test_replay_closed_burst_rides_out_a_full_queue():
+    # a burst larger than the queue: refused submissions (LUTC_EBUSY) are retried until admitted
+    s = _server(max_batch=4, max_wait_us=100, fake_latency_us=200, max_queue=16)
+    raw, out = _bufs(8)
+    r = s.replay([(0.0, i % 4, raw, out, False) for i in range(200)])
+    assert (r["status"] == 0).all() and s.stats()["completed"] == 200
+    s.close()
+
+
+def test_replay_rejects_a_bad_schedule_before_submitting():
+    s = _server()
+    raw, out = _bufs(8)
+    for bad in ([(0.01, 0, raw, out, False), (0.0, 0, raw, out, False)], [(-1.0, 0, raw, out, False)],
+                [(float("nan"), 0, raw, out, False)]):
+        with pytest.raises(lutc.LutcError) as e:
+            s.replay(bad)
+        assert e.value.status == _lib.LUTC_EINVAL
+    assert s.stats()["completed"] == 0
+    # an unknown sensor stops the schedule at that request; the ones before it complete
+    r = None
+    with pytest.raises(lutc.LutcError):
+        s.replay([(0.0, 0, raw, out, False), (0.0, 99, raw, out, False), (0.0, 1, raw, out, False)])
+    assert s.stats()["completed"] == 1
+    s.close()
