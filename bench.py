@@ -257,6 +257,130 @@ def run_reference(args, wl):
 
 # ----------------------------------------------------------------------------- the CUDA path
 
+def ncu_entry(workload: str, kernel: str, hash_key: str = "csrc"):
+    """The committed ncu summary entry of `kernel` on `workload`, if it was taken on this source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            e = json.load(f)[workload][kernel]
+        return e if e.get(hash_key) == csrc_hash(workload) else None
+    except Exception:
+        return None
+
+
+def smem_pipe(workload: str, kernel: str, pixels: int, measured_ms: float, sm_mhz: float | None, sms: int):
+    """The shared-memory pipe floor of a pass: its LSU shared-memory wavefronts per launch (committed ncu
+    capture on this source, scaled by pixels when captured on a smaller case) at one wavefront per SM
+    clock on every SM, against the measured duration."""
+    e = ncu_entry(workload, kernel, "smem_csrc")
+    if not e or not sm_mhz:
+        return None
+    wf = float(e["smem_wavefronts"]) / float(e["smem_captured_pixels"]) * pixels
+    floor_ms = wf / (sms * sm_mhz * 1e6) * 1e3
+    return {"wavefronts_per_launch": wf, "wavefronts_per_px": wf / pixels,
+            "floor_ms": floor_ms, "measured_ms": measured_ms, "frac_smem": floor_ms / measured_ms,
+            "rate": "1 wavefront per SM clock, %d SMs at the sampled median %.0f MHz" % (sms, sm_mhz),
+            "capture": e.get("smem_capture")}
+
+
+def fused_leg(lib, lutc, wl, raw, cd, out, wsb, device, steps: int, warmup: int, ws: int = 1):
+    """One lutc_correct_image step timed as CUDA-graph replays (clocks sampled meanwhile), as direct
+    C-ABI calls, and per phase from traced direct calls; returns the timings and the kernel family."""
+    import torch
+    import torch.distributed as dist
+    from paper_1505_05655_gb300._lib import LUTC_STRETCH
+
+    stream = torch.cuda.current_stream(device)
+    st = ctypes.c_void_p(stream.cuda_stream)
+    desc = lutc.raster_desc(raw, wl.bits)
+    flags = LUTC_STRETCH if wl.stretch else 0
+    pitch = out.stride(1) * out.element_size()
+
+    def call(s=st):
+        rc = lib.lutc_correct_image(ctypes.byref(desc), cd, flags, ctypes.c_void_p(out.data_ptr()), pitch,
+                                    ctypes.c_void_p(wsb.data_ptr()), wsb.numel(), s)
+        if rc:
+            raise RuntimeError("lutc_correct_image failed: %d" % rc)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize(device)
+
+    dev_id = None
+    try:
+        dev_id = str(torch.cuda.get_device_properties(device).uuid)
+        dev_id = dev_id if dev_id.startswith("GPU-") else "GPU-" + dev_id
+    except Exception:
+        dev_id = None
+    sampler = ClockSampler(dev_id)
+    for _ in range(max(3, warmup)):
+        call()
+    path = lutc.last_path()
+    barrier()
+    # One step captured in a CUDA graph (histogram clear, pass 1, scan, pass 2): replaying it keeps
+    # host launch latency out of the timed loop.  Every replay does the whole step's work.
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        call(ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream))
+    for _ in range(3):
+        graph.replay()
+
+    def timed(fn, k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1)
+
+    wall0 = time.time()
+    ms = timed(graph.replay, steps)
+    wall1 = time.time()
+    clocks = sampler.stop(wall0, wall1)
+    direct_ms = timed(call, steps)
+    phases = []
+    if wl.stretch:
+        k = min(steps, 200)
+        lutc.trace_enable(k)
+        timed(call, k)
+        phases = lutc.trace_read(k)
+        lutc.trace_enable(0)
+    del graph
+    return {"ms": ms, "direct_ms": direct_ms, "phases": phases, "path": path, "clocks": clocks, "steps": steps}
+
+
+def fused_roofline(wl, workload: str, phases, path: int, clocks, peak: float, peak_src: str, sms: int):
+    """Roofline of the dominant pass (HBM, algorithmic bytes over the traced mean duration) with the
+    shared-memory pipe floor of both passes beside it; (roofline, phases_ms)."""
+    from paper_1505_05655_gb300._lib import LUTC_PATH_TMA
+    avg = [statistics.fmean(p[i] for p in phases) for i in range(3)]
+    tma = path == LUTC_PATH_TMA
+    kern = ("k_tma_strip<hist>", "k_stretch", "k_tma_strip<apply>") if tma else \
+        ("k_strip_hist", "k_stretch", "k_strip_apply")
+    keys = ("pass1", "scan", "pass2")
+    alg = [2 * wl.pixels, 8 * wl.bands * (1 << wl.bits), 3 * wl.pixels]
+    dom = max(range(3), key=lambda i: avg[i])
+    ach = alg[dom] / (avg[dom] * 1e-3) / 1e9
+    mhz = clocks["sm_mhz"] if clocks else None
+    pipe = {k: smem_pipe(workload, k, wl.pixels, avg[i], mhz, sms) if tma else None
+            for i, k in ((0, "pass1"), (2, "pass2"))}
+    tr = ncu_traffic(keys[dom], workload) if tma else None
+    roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": tr, "kernel": "%s %s" % (keys[dom], kern[dom]),
+            "kernel_family": "tma" if tma else "strip (lutc_last_path)",
+            "l1tex": ncu_l1tex_busy(keys[dom], workload) if tma else None,
+            "peak_source": peak_src + " (copy bandwidth)", "alg_bytes_per_launch": alg[dom],
+            "traffic_GBs": tr / (avg[dom] * 1e-3) / 1e9 if tr else None,
+            "smem_pipe": pipe}
+    ph = {"pass1_hist": avg[0], "scan": avg[1], "pass2_apply": avg[2],
+          "pass1_GBs": alg[0] / (avg[0] * 1e-3) / 1e9, "pass2_GBs": alg[2] / (avg[2] * 1e-3) / 1e9,
+          "pass1_hbm_frac": alg[0] / (avg[0] * 1e-3) / 1e9 / peak,
+          "pass2_hbm_frac": alg[2] / (avg[2] * 1e-3) / 1e9 / peak}
+    return roof, ph
+
+
 def run_lutc(args, wl):
     import torch
     import torch.distributed as dist
@@ -272,6 +396,7 @@ def run_lutc(args, wl):
     from paper_1505_05655_gb300._lib import LUTC_STRETCH
 
     lib = lutc.lib()
+    n_sm = torch.cuda.get_device_properties(device).multi_processor_count
     # inputs: generated straight into pinned host memory (the end-to-end leg copies from there)
     shape = (wl.bands, wl.height, wl.width)
     raw_h = torch.empty(shape, dtype=torch.uint16, pin_memory=True)
@@ -288,63 +413,21 @@ def run_lutc(args, wl):
     st = ctypes.c_void_p(stream.cuda_stream)
     flags = LUTC_STRETCH if wl.stretch else 0
     pitch = out.stride(1) * out.element_size()
-    call = lambda: lib.lutc_correct_image(ctypes.byref(desc), cd, flags, ctypes.c_void_p(out.data_ptr()), pitch,
-                                          ctypes.c_void_p(wsb.data_ptr()), wsb.numel(), st)
+
+    def check(rc):
+        if rc:
+            raise RuntimeError("lutc_correct_image failed: %d" % rc)
+
+    call = lambda: check(lib.lutc_correct_image(ctypes.byref(desc), cd, flags, ctypes.c_void_p(out.data_ptr()), pitch,
+                                                ctypes.c_void_p(wsb.data_ptr()), wsb.numel(), st))
 
     def barrier():
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize(device)
 
-    dev_id = None
-    try:
-        dev_id = str(torch.cuda.get_device_properties(device).uuid)
-        dev_id = dev_id if dev_id.startswith("GPU-") else "GPU-" + dev_id
-    except Exception:
-        dev_id = None
-    sampler = ClockSampler(dev_id)
-
-    def check(rc):
-        if rc:
-            raise RuntimeError("lutc_correct_image failed: %d" % rc)
-
-    for _ in range(max(3, args.warmup)):
-        check(call())
-    barrier()
-    # One step captured in a CUDA graph (histogram clear, pass 1, scan, pass 2): replaying it keeps
-    # host launch latency out of the timed loop.  Every replay does the whole step's work.
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        cap = ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
-        check(lib.lutc_correct_image(ctypes.byref(desc), cd, flags, ctypes.c_void_p(out.data_ptr()), pitch,
-                                     ctypes.c_void_p(wsb.data_ptr()), wsb.numel(), cap))
-    for _ in range(3):
-        graph.replay()
-
-    def timed(fn, steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier()
-        e0.record(stream)
-        for _ in range(steps):
-            fn()
-        e1.record(stream)
-        barrier()
-        return e0.elapsed_time(e1)
-
-    wall0 = time.time()
-    ms = timed(graph.replay, args.steps)
-    wall1 = time.time()
-    clocks = sampler.stop(wall0, wall1)
-    # the same steps as direct C-ABI calls, and per-phase times from traced direct calls
-    direct_ms = timed(lambda: check(call()), args.steps)
-    phases = []
-    if wl.stretch:
-        k = min(args.steps, 200)
-        lutc.trace_enable(k)
-        timed(lambda: check(call()), k)
-        phases = lutc.trace_read(k)
-        lutc.trace_enable(0)
-    ms, direct_ms = max_over_ranks([ms, direct_ms], device)
+    leg = fused_leg(lib, lutc, wl, raw, cd, out, wsb, device, args.steps, args.warmup, ws)
+    ms, direct_ms = max_over_ranks([leg["ms"], leg["direct_ms"]], device)
     ms_step = ms / args.steps
     value = whole_job_rate(wl.pixels, ws, args.steps, ms)
 
@@ -361,31 +444,16 @@ def run_lutc(args, wl):
                       "direct_calls: the same steps as C-ABI calls" % args.steps)
     line["direct_calls"] = {"value": wl.pixels * ws * args.steps / (direct_ms * 1e-3) / 1e9, "unit": UNIT,
                             "ms_per_step": direct_ms / args.steps}
-    if phases:
-        avg = [statistics.fmean(p[i] for p in phases) for i in range(3)]
-        tma = wl.width >= 256 and raw.data_ptr() % 16 == 0 and (raw.stride(1) * 2) % 16 == 0
-        names = (["pass1 k_tma_strip<hist>", "scan k_stretch", "pass2 k_tma_strip<apply>"] if tma
-                 else ["pass1 k_strip_hist", "scan k_stretch", "pass2 k_strip_apply"])
-        alg = [2 * wl.pixels, 8 * wl.bands * (1 << wl.bits), 3 * wl.pixels]
-        dom = max(range(3), key=lambda i: avg[i])
-        ach = alg[dom] / (avg[dom] * 1e-3) / 1e9
-        line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                            "traffic": ncu_traffic(names[dom].split()[0], wl.name), "kernel": names[dom],
-                            "l1tex": ncu_l1tex_busy(names[dom].split()[0], wl.name),
-                            "peak_source": peak_src + " (copy bandwidth)",
-                            "alg_bytes_per_launch": alg[dom]}
-        tr = line["roofline"]["traffic"]
-        # the same launch's DRAM bytes from the committed ncu capture over its live duration
-        line["roofline"]["traffic_GBs"] = tr / (avg[dom] * 1e-3) / 1e9 if tr else None
-        line["phases_ms"] = {"pass1_hist": avg[0], "scan": avg[1], "pass2_apply": avg[2],
-                             "pass1_GBs": alg[0] / (avg[0] * 1e-3) / 1e9,
-                             "pass2_GBs": alg[2] / (avg[2] * 1e-3) / 1e9}
+    if leg["phases"]:
+        line["roofline"], line["phases_ms"] = fused_roofline(wl, wl.name, leg["phases"], leg["path"], leg["clocks"],
+                                                             peak, peak_src, n_sm)
     else:
         ach = wl.pixels * 4 / (ms_step * 1e-3) / 1e9
         line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                             "traffic": ncu_traffic("pass2", wl.name), "kernel": "detector-only apply",
+                            "kernel_family": {1: "tma", 2: "strip"}.get(leg["path"], "none"),
                             "peak_source": peak_src + " (copy bandwidth)", "alg_bytes_per_launch": 4 * wl.pixels}
-    line["clocks"] = clocks
+    line["clocks"] = leg["clocks"]
     line["gpu_launches"] = (3 if wl.stretch else 1) * args.steps  # in the graph: pass 1, scan, pass 2
     status = ctypes.c_int(-1)
     lib.lutc_device_status(ctypes.byref(status), st)
@@ -488,6 +556,10 @@ def run_lutc(args, wl):
         del raw, out, raw_h, out_h
         gc.collect()
         torch.cuda.empty_cache()
+        # the large 14-bit scene on the same kernels, timed and checked against the oracle in full
+        line["large14"] = run_large14(sub)
+        gc.collect()
+        torch.cuda.empty_cache()
         b = run_batch(sub)
         line["batched"] = {"value": b["value"], "unit": UNIT, "ms_per_step": b["ms_per_step"],
                            "images": b["config"]["images"], "pixels_per_step": b["config"]["pixels_per_step"],
@@ -497,23 +569,73 @@ def run_lutc(args, wl):
         gc.collect()
         torch.cuda.empty_cache()
         v = serve_in_child(args)
-        line["served"] = {"saturation_gpx_s": v["saturation"]["gpx_s"],
-                          "vs_fused_single": v["saturation"]["gpx_s"] / value,
-                          "latency_ms": {r: {"p50": d["p50_ms"], "p99": d["p99_ms"], "gpx_s": d["gpx_s"],
-                                             "mean_batch": d["mean_batch"], "tail": d["tail"]}
-                                         for r, d in v["latency"].items()},
-                          "outputs_equal_single_calls": v["outputs_equal_single_calls"],
-                          "host_requests": {"saturation_gpx_s": v["host_requests"]["saturation"]["gpx_s"],
-                                            "p50_ms_200": v["host_requests"]["latency_200"]["p50_ms"],
-                                            "p99_ms_200": v["host_requests"]["latency_200"]["p99_ms"],
-                                            "tail_200": v["host_requests"]["latency_200"]["tail"],
-                                            "outputs_equal_single_calls":
-                                                v["host_requests"]["outputs_equal_single_calls"]},
-                          "config": v["config"]["workload"]}
+        line["served"] = served_summary(v, value)
         line["fit"] = run_fit(sub)
         line["demosaic"] = run_demosaic(sub)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_large14(args):
+    """The large 14-bit scene (3 x 24000 x 24000, dead columns, saturated pixels) on the fused path:
+    graph-timed steps, phases, both passes against HBM and the shared-memory pipe, clocks during its
+    own timed region, and every output pixel against the oracle (all host threads)."""
+    import torch
+    import synth
+    import paper_1505_05655_gb300 as lutc
+
+    wl = synth.WORKLOADS["large14"]
+    device = torch.device("cuda", torch.cuda.current_device())
+    lib = lutc.lib()
+    n_sm = torch.cuda.get_device_properties(device).multi_processor_count
+    t = time.perf_counter()
+    raw_np, A, G, O = gen_inputs(wl, 0)
+    gen_s = time.perf_counter() - t
+    raw = torch.from_numpy(raw_np).to(device)
+    dA, dG, dO = (torch.from_numpy(a).to(device) for a in (A, G, O))
+    out = torch.empty(raw.shape, dtype=torch.uint8, device=device)
+    desc = lutc.raster_desc(raw, wl.bits)
+    cd = lutc.coeff_descs(dA, dG, dO)
+    wsb = torch.empty(max(256, lutc.correct_image_workspace(desc)), dtype=torch.uint8, device=device)
+    steps = max(20, args.steps)
+    leg = fused_leg(lib, lutc, wl, raw, cd, out, wsb, device, steps, 3)
+    ms_step = leg["ms"] / steps
+    peak, peak_src = peaks()
+    roof, ph = fused_roofline(wl, wl.name, leg["phases"], leg["path"], leg["clocks"], peak, peak_src, n_sm)
+    res = {"config": workload_config(wl), "steps": steps, "ms_per_step": ms_step,
+           "value": wl.pixels / (ms_step * 1e-3) / 1e9, "unit": UNIT,
+           "hbm_frac_step": wl.pixels * 5 / (ms_step * 1e-3) / 1e9 / peak,
+           "direct_calls": {"value": wl.pixels * steps / (leg["direct_ms"] * 1e-3) / 1e9,
+                            "ms_per_step": leg["direct_ms"] / steps},
+           "phases_ms": ph, "roofline": roof, "clocks": leg["clocks"],
+           "timing": "CUDA events around %d replays of a CUDA graph holding one step; inputs larger than L2" % steps}
+    if not args.no_cpu_baseline:
+        got = out.cpu().numpy()
+        threads = max(1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1))
+        t = time.perf_counter()
+        ref = cpu_baseline_threads(wl, raw_np, A, G, O, threads)
+        dt = time.perf_counter() - t
+        res["parity"] = {"bit_exact_vs_oracle": bool(np.array_equal(ref, got)), "pixels_compared": int(ref.size)}
+        res["cpu_baseline"] = {"value": wl.pixels / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": "the whole large14 workload on %d threads, %.1f s (inputs generated in "
+                                         "%.1f s)" % (threads, dt, gen_s)}
+    del raw, out, wsb
+    return res
+
+
+def served_summary(v, fused_value: float) -> dict:
+    """The bench line's summary of the serving run (`--workload serve`)."""
+    keep = ("p50_ms", "p99_ms", "gpx_s", "req_s", "offered_req_s", "mean_batch", "requests", "failed", "tail")
+    sat = v["saturation"]
+    return {"saturation_gpx_s": sat["gpx_s"], "vs_fused_single": sat["gpx_s"] / fused_value,
+            "saturation": {k: sat.get(k) for k in keep},
+            "latency_ms": {r: {k: d.get(k) for k in keep} for r, d in v["latency"].items()},
+            "outputs_equal_single_calls": v["outputs_equal_single_calls"],
+            "host_requests": {"saturation_gpx_s": v["host_requests"]["saturation"]["gpx_s"],
+                              "saturation": {k: v["host_requests"]["saturation"].get(k) for k in keep},
+                              "latency_200": {k: v["host_requests"]["latency_200"].get(k) for k in keep},
+                              "outputs_equal_single_calls": v["host_requests"]["outputs_equal_single_calls"]},
+            "load_generator": v["config"].get("load_generator"), "config": v["config"]["workload"]}
 
 
 def run_plain(lutc, raw, dA, dG, dO, wl, device, stream, steps):
@@ -727,8 +849,9 @@ def run_batch(args):
 
 
 def run_serve(args):
-    """Open-loop Poisson load on the request loop; p50/p99 latency per load and saturation throughput."""
-    import threading
+    """Open-loop Poisson loads on the request loop, driven by the library's native replay thread
+    (lutc_server_replay): p50/p99 latency per load, saturation throughput and its latency, loads at
+    fractions of the saturated request rate, and host-memory requests."""
     import torch
     import synth
     import paper_1505_05655_gb300 as lutc
@@ -766,80 +889,52 @@ def run_serve(args):
                 pool_host.append((sid, raw_h[:, :, :W].numpy(), out_h[:, :, :W].numpy(), B * H * W, raw_h, out_h))
     rng = np.random.default_rng(synth.SERVE_SEED)
     used_dev, used_host = set(), set()
+    mean_px = float(np.mean([p[3] for p in pool]))
 
     def drive(rate, n, closed=False, host=False):
-        # the earlier phases' garbage (page-locked buffers among it) is freed here, not by a collection
-        # that would stall this process in the middle of a load
-        gc.collect()
+        gc.collect()  # nothing of the earlier loads is left for the collector to find during this one
         used = used_host if host else used_dev
         src = pool_host if host else pool
         picks = rng.integers(0, len(src), n)
-        gaps = rng.exponential(1.0 / rate, n) if rate else np.zeros(n)
-        sched = np.cumsum(gaps)
-        tickets = [None] * n
-        infos = [None] * n
-        t0 = time.monotonic() + 0.01
-
-        def submitter():
-            for i in range(n):
-                if not closed:
-                    dt = t0 + sched[i] - time.monotonic()
-                    if dt > 0:
-                        time.sleep(dt)
-                sid, raw, out = src[picks[i]][:3]
-                while True:
-                    rc, t = server.try_submit(sid, raw, out, host=host)
-                    if rc == 0:
-                        break
-                    time.sleep(0.0002)  # queue full under a closed-loop burst
-                tickets[i] = t
-
-        if closed:
-            # saturation: the whole burst queued first, then collected (a submitting thread racing the
-            # collecting one for the interpreter let the queue run dry: the load generator, not the
-            # server, then set the rate)
-            submitter()
-            for i in range(n):
-                infos[i] = server.wait(tickets[i])
-        else:
-            th = threading.Thread(target=submitter)
-            th.start()
-            for i in range(n):
-                while tickets[i] is None:
-                    time.sleep(0.0001)
-                infos[i] = server.wait(tickets[i])
-            th.join()
-        lat = np.array([infos[i].done_s - (t0 + sched[i] if not closed else infos[i].submit_s) for i in range(n)])
-        px = sum(src[j][3] for j in picks)
-        span = max(i.done_s for i in infos) - min(i.submit_s for i in infos)
-        bad = sum(1 for i in infos if i.status != 0)
+        at = np.zeros(n) if closed else np.cumsum(rng.exponential(1.0 / rate, n))
+        r = server.replay([(float(at[i]), src[j][0], src[j][1], src[j][2], host) for i, j in enumerate(picks)])
         used.update(int(j) for j in picks)
-        prep = np.array([i.launched_s - i.start_s for i in infos])
-        run = np.array([i.done_s - i.launched_s for i in infos])
-        # where the slowest 1 % spent their time: late submission (the load generator), the batch
-        # window and admission (submit -> start), batch preparation (start -> launched), the device
+        # closed burst: latency from each request's own submission; open loop: from its scheduled arrival,
+        # so any lateness of the hand-over (submit_lag) counts against the request
+        t_from = r["submit_s"] if closed else r["scheduled_s"]
+        lat = r["done_s"] - t_from
+        px = sum(src[j][3] for j in picks)
+        span = r["done_s"].max() - r["submit_s"].min()
+        prep = r["launched_s"] - r["start_s"]
+        run = r["done_s"] - r["launched_s"]
+        lag = r["submit_s"] - r["scheduled_s"]
+        # where the slowest 1 % spent their time: late hand-over by the load generator, the batch window
+        # and admission (submit -> start), batch preparation (start -> launched), the device
         p99 = float(np.percentile(lat, 99))
-        slow = [k for k in range(n) if lat[k] >= p99]
-        lag = [infos[k].submit_s - (t0 + sched[k]) if not closed else 0.0 for k in slow]
+        slow = lat >= p99
         stage = lambda xs: round(float(np.median(xs)) * 1e3, 3)
-        tail = dict(requests=len(slow), max_ms=round(float(lat.max()) * 1e3, 3),
-                    submit_lag_ms=stage(lag), queue_ms=stage([infos[k].start_s - infos[k].submit_s for k in slow]),
-                    prep_ms=stage([prep[k] for k in slow]), launch_to_done_ms=stage([run[k] for k in slow]),
-                    cache_misses=int(sum(infos[k].cache_miss for k in slow)),
-                    first_s=round(float(min(infos[k].submit_s for k in slow) - t0), 3),
-                    last_s=round(float(max(infos[k].submit_s for k in slow) - t0), 3))
-        return dict(p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=p99 * 1e3,
-                    gpx_s=px / span / 1e9, mean_batch=float(np.mean([i.batch_size for i in infos])),
-                    requests=n, failed=bad, offered_gpx_s=(px / n) * rate / 1e9 if rate else None,
+        tail = dict(requests=int(slow.sum()), max_ms=round(float(lat.max()) * 1e3, 3),
+                    submit_lag_ms=0.0 if closed else stage(lag[slow]),
+                    submit_lag_max_ms=0.0 if closed else round(float(lag.max()) * 1e3, 3),
+                    queue_ms=stage((r["start_s"] - r["submit_s"])[slow]), prep_ms=stage(prep[slow]),
+                    launch_to_done_ms=stage(run[slow]), cache_misses=int(r["cache_miss"][slow].sum()))
+        return dict(p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=p99 * 1e3, gpx_s=px / span / 1e9,
+                    req_s=n / span, offered_req_s=None if closed else rate,
+                    offered_gpx_s=None if closed else mean_px * rate / 1e9,
+                    mean_batch=float(np.mean(r["batch_size"])), requests=n, failed=int((r["status"] != 0).sum()),
                     batch_prep_ms=float(np.median(prep) * 1e3), launch_to_done_ms=float(np.median(run) * 1e3),
-                    tail=tail)
+                    latency_from="submission" if closed else "scheduled arrival", tail=tail)
 
     warm = drive(400, 200)  # first requests of every sensor upload its coefficients
+    sat = drive(0, max(2000, 2 * args.steps), closed=True)
     loads = {}
-    # at least 2000 requests per load (p99 over enough samples): 40 s at 50 req/s
+    # the configured open-loop loads, at least 2000 requests each (40 s at 50 req/s)
     for rate, n in ((50, max(2000, args.steps // 4)), (200, max(2000, args.steps)), (800, max(2000, 2 * args.steps))):
         loads[str(rate)] = drive(rate, n)
-    sat = drive(0, max(500, 2 * args.steps), closed=True)
+    # loads high enough to batch for real: fractions of the saturated request rate, ~1 s each
+    for frac in (0.25, 0.5, 0.75):
+        rate = frac * sat["req_s"]
+        loads["%d%% of saturation" % round(100 * frac)] = drive(rate, int(max(2000, min(60000, rate))))
     # requests from pinned host memory: staged in and out by the server (copies inside each request's latency)
     host_sat = drive(0, max(300, args.steps), closed=True, host=True)
     host_200 = drive(200, max(300, args.steps // 2), host=True)
@@ -865,9 +960,12 @@ def run_serve(args):
             "warmup": warm["requests"], "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": "serve: %d sensors from the batch mixture, %d pool rasters each, device-resident; "
-                                   "Poisson arrivals 50/200/800 req/s; budget 40 GiB; a request launches at once on "
-                                   "an idle device, else batches <= 32 requests or 2 ms, 4 streams"
-                                   % (nsens, pool_per_sensor), "row_align_bytes": args.row_align,
+                                   "Poisson arrivals 50/200/800 req/s and 25/50/75 %% of the saturated request "
+                                   "rate; budget 40 GiB; a request launches at once on an idle device, else batches "
+                                   "<= 32 requests or 2 ms, 4 streams" % (nsens, pool_per_sensor),
+                       "row_align_bytes": args.row_align, "mean_request_px": mean_px,
+                       "load_generator": "lutc_server_replay: arrival times drawn up front, submitted on schedule "
+                                         "by a native thread, collected by the calling thread",
                        "l2": "inputs larger than L2 (pool %.1f GB)" % (sum(p_[3] for p_ in pool) * 2 / 1e9)},
             "latency": loads, "saturation": sat, "warmup_with_cache_misses": warm, "server": st,
             "outputs_equal_single_calls": exact,
@@ -899,7 +997,7 @@ def _selected(args, name: str) -> bool:
 
 
 def fp64_peak_tflops(device) -> tuple[float, str]:
-    """fp64 FMA-pipe peak: SMs x 2 fp64 FMA per clock x 2 flops x maximum SM clock."""
+    """fp64 FMA-pipe peak derived from the unit count: SMs x 2 fp64 FMA per clock x 2 flops x maximum SM clock."""
     import torch
     sms = torch.cuda.get_device_properties(device).multi_processor_count
     mhz = 2070.0
@@ -912,6 +1010,41 @@ def fp64_peak_tflops(device) -> tuple[float, str]:
     return sms * 2 * 2 * mhz * 1e6 / 1e12, "%d SMs x 2 fp64 FMA/clk x 2 flop x %.0f MHz" % (sms, mhz)
 
 
+def fp64_peak_measured(device) -> dict:
+    """The fp64 FMA rate measured on this device: lutc_probe_fp64_fma (register-only FMA chains, 8 blocks
+    of 256 threads per SM), timed with CUDA events over 5 launches after 2 warm-ups, clocks sampled."""
+    import torch
+    import paper_1505_05655_gb300 as lutc
+    lib = lutc.lib()
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    stream = torch.cuda.current_stream(device)
+    st = ctypes.c_void_p(stream.cuda_stream)
+    blocks, iters = sms * 8, 1 << 14
+    sink = torch.empty(blocks * 256, dtype=torch.float64, device=device)
+    fmas = ctypes.c_longlong(0)
+    launch = lambda: lutc.check(lib.lutc_probe_fp64_fma(blocks, iters, ctypes.c_void_p(sink.data_ptr()),
+                                                        ctypes.byref(fmas), st), "lutc_probe_fp64_fma")
+    for _ in range(2):
+        launch()
+    torch.cuda.synchronize(device)
+    sampler = ClockSampler(None)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    wall0 = time.time()
+    e0.record(stream)
+    for _ in range(5):
+        launch()
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    wall1 = time.time()
+    clocks = sampler.stop(wall0, wall1)
+    ms = e0.elapsed_time(e1) / 5
+    tflops = 2 * fmas.value / (ms * 1e-3) / 1e12
+    mhz = clocks["sm_mhz"] if clocks else None
+    return {"tflops": tflops, "ms_per_launch": ms, "fmas_per_launch": fmas.value, "clocks": clocks,
+            "fma_per_sm_per_clock": fmas.value / (ms * 1e-3) / (sms * mhz * 1e6) if mhz else None,
+            "how": "lutc_probe_fp64_fma: %d blocks x 256 threads x 8 chains x %d FMAs on registers" % (blocks, iters)}
+
+
 def run_fit(args):
     """Per-detector least-squares fit: the paper's shape (6 lines x 6000 detectors) and a large calibration."""
     import torch
@@ -922,7 +1055,9 @@ def run_fit(args):
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     stream = torch.cuda.current_stream(device)
-    peak, peak_how = fp64_peak_tflops(device)
+    derived, derived_how = fp64_peak_tflops(device)
+    probe = fp64_peak_measured(device)
+    peak, peak_how = probe["tflops"], "measured: " + probe["how"]
 
     def timed(fn, steps):
         torch.cuda.synchronize(device)
@@ -970,6 +1105,7 @@ def run_fit(args):
                                "roofline": {"bound": "alu", "achieved": flops / (gms * 1e-3) / 1e12, "peak": peak,
                                             "unit": "TFLOP/s (fp64)", "frac": flops / (gms * 1e-3) / 1e12 / peak,
                                             "flops_per_sample": 2 * (order + 1), "peak_source": peak_how,
+                                            "frac_of_derived_peak": flops / (gms * 1e-3) / 1e12 / derived,
                                             "fp64_issue_frac": issue / (gms * 1e-3) / 1e12 / (peak / 2)}}
             if name == "paper" and rank == 0 and not args.no_cpu_baseline:
                 import oracle
@@ -990,6 +1126,7 @@ def run_fit(args):
                                              "max_rel_diff_scaled_coef": float(rel.max()) if rel.size else 0.0}
         res[name] = {"lines": n, "detectors": ncols, "bits": bits, "orders": per,
                      "x_bytes": n * ncols * 2}
+    res["fp64_peak"] = dict(probe, derived_tflops=derived, derived_how=derived_how)
     return res
 
 

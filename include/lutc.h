@@ -296,6 +296,19 @@ LUTC_API int lutc_submit(int task, const char* params, const void* const* inputs
  */
 LUTC_API int lutc_device_info(char* xml, size_t capacity, size_t* needed);
 
+/**
+ * Measurement aid beside the device listing: the listing states the clock and
+ * the multiprocessor count, not the fp64 fused multiply-add rate that bounds
+ * the least-squares fit (Section III-B).  Launches `blocks` (1 .. 2^20) blocks
+ * of 256 threads on `stream`, each thread running `iters` (1 .. 2^24) rounds
+ * of 8 independent fp64 FMA chains on registers and storing one double to
+ * sink[block * 256 + thread] (device memory, blocks * 256 doubles, caller
+ * owned).  *fmas (may be NULL) receives the FMAs the launch performs; timing
+ * the launch with CUDA events on `stream` gives the device's FMA rate.
+ * Asynchronous.  Returns LUTC_OK, LUTC_EINVAL or LUTC_ECUDA.
+ */
+LUTC_API int lutc_probe_fp64_fma(int blocks, long long iters, double* sink, long long* fmas, lutc_stream stream);
+
 /* ------------------------------------------------------------------------
  * The paper's transport (Section II, Fig. 3): a TCP server in front of
  * lutc_submit.

@@ -141,6 +141,7 @@ SIGNATURES = {
                                  ctypes.POINTER(ctypes.c_float)]),
     "lutc_get_tuning": (_I, [_I, ctypes.POINTER(Tuning)]),
     "lutc_last_path": (_I, [ctypes.POINTER(_I)]),
+    "lutc_probe_fp64_fma": (_I, [_I, ctypes.c_longlong, _P, ctypes.POINTER(ctypes.c_longlong), _P]),
     "lutc_trace_read": (_I, [ctypes.POINTER(ctypes.c_float), _I]),
 }
 

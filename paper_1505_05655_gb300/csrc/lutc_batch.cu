@@ -13,6 +13,11 @@
 //   per image band) -> pass 2 (all stretch images) -> detector-only pass (all
 //   uint16 images) -> images the TMA kernels cannot take, one by one
 //
+// The two pass-1 launches balance themselves at run time as well: each block
+// claims its run a granule at a time and, once done, steals the upper half of
+// the largest run left (lutc_tma.cu); the runs start from the planned
+// boundaries, copied into place on the device before each launch.
+//
 // optionally captured once in a CUDA graph and replayed (lutc_batch_correct:
 // planned, run once and released in one call).  All device data (job table,
 // tensor maps, coefficient pointers, tables) lives in the caller's workspace:
@@ -43,13 +48,12 @@ constexpr int kSmallBits = 12;
 // row's cost is modelled as its valid columns plus kRowOverhead: measured on GB300, a row of a
 // narrow right-edge strip costs about as much as a full one (the tile's round trip through the
 // shared-memory ring dominates), so the overhead term is a full strip's width.
-constexpr int kMaxGrid = 2048;  // blocks of a launch, or chunks of a claimed launch's partition
+constexpr int kMaxGrid = 2048;  // blocks of a launch
 constexpr int kLaunches = 4;  // pass 1 (small tables), pass 1 (large tables), pass 2, detector only
-// Pass 1 of the small tables cuts its units into about kChunksPerBlock chunks per block, which the
-// blocks claim at run time: measured, its blocks left the SMs 20 % idle with one precomputed run each
-// (a model cannot price every image of a mix), and blocks that finish early now take more.  Claiming
-// costs a histogram flush per chunk, cheap at <= 12 bits; the other launches keep one run per block.
-constexpr int kChunksPerBlock = 4;
+// Pass 1's launches steal work (measured: with one precomputed run per block the SMs of the small
+// tables' launch sat 20 % idle -- a model cannot price every image of a mix); each needs its blocks'
+// initial runs and the live copy the blocks claim from, kMaxGrid packed words each.
+constexpr int kStealLaunches = 2;
 constexpr int64_t kRowOverhead = 2048;
 
 void partition(const JobDesc* J, int n, int SW, int grid, int64_t* starts)
@@ -93,7 +97,7 @@ struct Plan {
     int ns = 0, nd = 0, nbands_s = 0, nbands_d = 0;
     int ns_small = 0;  // stretch jobs of <= kSmallBits bits, placed first in the job table
     size_t off_sjobs = 0, off_djobs = 0, off_coef = 0, off_maps = 0, off_tables = 0, off_part = 0;
-    size_t off_ctr = 0;  // int32 chunk counter of the claimed launch, zeroed at the start of every run
+    size_t off_steal = 0;  // [kStealLaunches][2][kMaxGrid] uint64: initial runs, then the live runs
     size_t off_hist = 0, off_S = 0, off_lohi = 0, off_fb = 0, total = 0;
     size_t hist_bytes = 0, S_bytes = 0;
     int s_max_bits = 8, d_max_bits = 8;
@@ -162,8 +166,8 @@ int make_plan(const lutc_job* jobs, int n, Plan& p)
     o = align_up(o + sizeof(TableDesc) * p.nbands_s, 256);
     p.off_part = o;
     o = align_up(o + sizeof(int64_t) * kLaunches * (kMaxGrid + 1), 256);
-    p.off_ctr = o;
-    o = align_up(o + sizeof(int32_t), 256);
+    p.off_steal = o;
+    o = align_up(o + sizeof(uint64_t) * kStealLaunches * 2 * kMaxGrid, 256);
     p.off_hist = o;
     p.hist_bytes = (size_t)hist_elems * 8;
     o = align_up(o + p.hist_bytes, 256);
@@ -196,7 +200,7 @@ struct lutc_batch_st {
     int64_t s_units_small = 0;  // units of the first ns_small stretch jobs
     int small_max_bits = 8;
     int grid[kLaunches] = {0, 0, 0, 0};
-    int nchunks0 = 0;  // chunks of the claimed launch (pass 1, small tables)
+    bool steal = false;  // pass 1 steals work (unit numbers fit the packed runs)
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -234,13 +238,12 @@ int enqueue(lutc_batch b, cudaStream_t st, cudaEvent_t* tr)
         if ((rc = cuda_status(cudaMemsetAsync(L.hist, 0, p.hist_bytes, st)))) return rc;
         // pass 1 in two launches: small histograms (more blocks per SM), then the rest
         const int64_t* part = reinterpret_cast<const int64_t*>(b->ws + p.off_part);
+        uint64_t* steal = reinterpret_cast<uint64_t*>(b->ws + p.off_steal);  // [launch][initial | live][block]
         BatchLaunch L1 = L;
         L1.njobs = p.ns_small;
         L1.max_bits = b->small_max_bits;
         L1.units = b->s_units_small;
         L1.starts = part;
-        L1.nchunks = b->nchunks0;
-        L1.counter = reinterpret_cast<int*>(b->ws + p.off_ctr);
         L1.grid = b->grid[0];
         BatchLaunch L2 = L;
         L2.jobs = L.jobs + p.ns_small;
@@ -250,10 +253,20 @@ int enqueue(lutc_batch b, cudaStream_t st, cudaEvent_t* tr)
         L2.units = b->s_units - b->s_units_small;
         L2.starts = part + (kMaxGrid + 1);
         L2.grid = b->grid[1];
-        if (L1.njobs > 0 && ((rc = cuda_status(cudaMemsetAsync(L1.counter, 0, sizeof(int32_t), st))) ||
-                             (rc = tma_batch_pass(L1, kModeHist, tc, bps, st))))
-            return rc;
-        if (L2.njobs > 0 && (rc = tma_batch_pass(L2, kModeHist, tc, bps, st))) return rc;
+        BatchLaunch* P1[kStealLaunches] = {&L1, &L2};
+        for (int l = 0; l < kStealLaunches; ++l) {
+            BatchLaunch& Lp = *P1[l];
+            if (Lp.njobs <= 0) continue;
+            if (b->steal) {
+                // every run back at its planned start (the previous run left them used up)
+                uint64_t* init = steal + (size_t)l * 2 * kMaxGrid;
+                Lp.ranges = reinterpret_cast<unsigned long long*>(init + kMaxGrid);
+                if ((rc = cuda_status(cudaMemcpyAsync(Lp.ranges, init, sizeof(uint64_t) * Lp.grid,
+                                                      cudaMemcpyDeviceToDevice, st))))
+                    return rc;
+            }
+            if ((rc = tma_batch_pass(Lp, kModeHist, tc, bps, st))) return rc;
+        }
         if (tr) cudaEventRecord(tr[1], st);
         if ((rc = stretch_batch(reinterpret_cast<const TableDesc*>(b->ws + p.off_tables), p.nbands_s, L.hist,
                                 b->ws + p.off_S, reinterpret_cast<int32_t*>(b->ws + p.off_lohi), st)))
@@ -428,9 +441,15 @@ extern "C" int lutc_batch_create(const lutc_job* jobs, int n, const lutc_batch_c
                 g = std::min(g, kMaxGrid);
             }
             b->grid[l] = g;
-            int parts = std::max(g, 1);
-            if (l == 0 && L[l].n > 0) parts = b->nchunks0 = std::min(g * kChunksPerBlock, kMaxGrid);
-            partition(L[l].J, L[l].n, SW, parts, part + (size_t)l * (kMaxGrid + 1));
+            partition(L[l].J, L[l].n, SW, std::max(g, 1), part + (size_t)l * (kMaxGrid + 1));
+        }
+        // pass 1's initial runs as packed (start << 32 | end) words, when every unit number fits
+        b->steal = b->s_units < kStealMaxUnits;
+        uint64_t* steal = reinterpret_cast<uint64_t*>(b->blob.data() + p.off_steal);
+        for (int l = 0; l < kStealLaunches && b->steal; ++l) {
+            const int64_t* st0 = part + (size_t)l * (kMaxGrid + 1);
+            for (int k = 0; k < b->grid[l]; ++k)
+                steal[(size_t)l * 2 * kMaxGrid + k] = ((uint64_t)st0[k] << 32) | (uint64_t)st0[k + 1];
         }
     }
     if (p.off_hist > 0) {

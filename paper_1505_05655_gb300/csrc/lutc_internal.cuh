@@ -106,10 +106,10 @@ struct BatchLaunch {
     int32_t max_bits;
     int64_t unit_offset;      // first unit of the launch (jobs[0].unit_begin)
     int64_t units;
-    const int64_t* starts;    // device [grid + 1]: block k walks units [starts[k], starts[k + 1]); with a
-                              // counter, [nchunks + 1] chunk boundaries that blocks claim at run time
-    int32_t nchunks = 0;
-    int* counter = nullptr;   // pass 1 only: chunks claimed so far, zero before the launch (or nullptr)
+    const int64_t* starts;    // device [grid + 1]: block k walks units [starts[k], starts[k + 1])
+    unsigned long long* ranges = nullptr;  // pass 1 only: [grid] packed (next << 32 | end) runs the blocks
+                              // claim from and steal from, set to starts[] before the launch (or nullptr:
+                              // static runs)
     int32_t grid;
     unsigned long long* hist;
     const uint8_t* S;
@@ -123,6 +123,8 @@ int tma_preload();     // loads every TMA kernel variant, caches occupancies
 int tables_preload();  // loads the scan kernels
 int tma_batch_pass(const BatchLaunch& b, int mode, int column_threads, int blocks_per_sm, cudaStream_t st);
 // Blocks of a batch launch (SMs x resident blocks, capped by blocks_per_sm when > 0); 0 on error.
+// Stealing launches pack unit numbers in 32 bits: their units must stay below this.
+constexpr int64_t kStealMaxUnits = ((int64_t)1 << 32) - ((int64_t)1 << 20);
 int tma_batch_grid(int mode, int column_threads, int max_bits, int blocks_per_sm);
 int launch_stretch(const unsigned long long* hist, int bands, int bits, uint8_t* S, int32_t* lohi, cudaStream_t st);
 int stretch_batch(const TableDesc* tables, int ntables, const unsigned long long* hist, uint8_t* S, int32_t* lohi,

@@ -271,3 +271,45 @@ extern "C" int lutc_device_info(char* xml, size_t capacity, size_t* needed)
     memcpy(xml, doc.c_str(), doc.size() + 1);
     return LUTC_OK;
 }
+
+// ---------------------------------------------------------------------------
+// fp64 FMA rate probe: the device properties above state the clock and the
+// multiprocessor count, not how many fp64 fused multiply-adds a
+// multiprocessor issues per clock; this kernel measures it.  Each thread
+// runs 8 independent dependency chains of fma() on registers (no memory
+// traffic until the one store of its result), so the fp64 pipe's issue rate
+// is the only bound once enough warps are resident.
+// ---------------------------------------------------------------------------
+namespace lutc {
+namespace probe {
+
+constexpr int kProbeThreads = 256;
+constexpr int kProbeChains = 8;
+
+__global__ void __launch_bounds__(kProbeThreads) k_probe_fp64(long long iters, double b, double c, double* sink)
+{
+    double a[kProbeChains];
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) a[k] = (double)(threadIdx.x + k) * 1e-3;
+    for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kProbeChains; ++k) a[k] = fma(a[k], b, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) s += a[k];
+    sink[(size_t)blockIdx.x * kProbeThreads + threadIdx.x] = s;
+}
+
+}  // namespace probe
+}  // namespace lutc
+
+extern "C" int lutc_probe_fp64_fma(int blocks, long long iters, double* sink, long long* fmas, lutc_stream stream)
+{
+    if (blocks < 1 || blocks > (1 << 20) || iters < 1 || iters > (1ll << 24) || !sink) return LUTC_EINVAL;
+    // b and c chosen so that every chain stays finite and normal: a -> a * b + c converges to c / (1 - b)
+    using namespace lutc::probe;
+    k_probe_fp64<<<blocks, kProbeThreads, 0, (cudaStream_t)stream>>>(iters, 0.999999, 1e-6, sink);
+    if (fmas) *fmas = (long long)blocks * kProbeThreads * kProbeChains * iters;
+    return lutc::cuda_status(cudaGetLastError());
+}

@@ -69,7 +69,11 @@ constexpr int kRingBytes = kStages * kTileBytes;
 // mbarriers after the ring (full and empty per stage, one consumer barrier), then the table
 constexpr int kBarRegion = ((2 * kStages + 1) * 8 + 127) / 128 * 128;
 constexpr int kTableOffset = kRingBytes + kBarRegion;
-static_assert((2 * kStages + 1) * 8 + kStages * 4 <= kBarRegion, "barrier region (barriers, per-stage chunk ids)");
+static_assert((2 * kStages + 1) * 8 + kStages * 12 <= kBarRegion, "barrier region (barriers, per-stage tile units)");
+// Work stealing (batch pass 1): a block claims kStealGranule tiles' worth of units of its own run at a
+// time, and a run with fewer than two granules left is not stolen from.
+constexpr int kStealGranule = 8;
+constexpr int kStealTries = 8;  // lost compare-and-swap races before a block stops looking for work
 static_assert(kTableOffset % 128 == 0, "table alignment");
 
 enum Mode { kHist = kModeHist, kHistGlobal = kModeHistGlobal, kApplyStretch = kModeApplyStretch,
@@ -98,12 +102,11 @@ struct BatchArgs {
     int64_t unit_offset;  // first unit of this launch (its jobs' unit_begin are absolute)
     int64_t units;
     int64_t units_per_block;
-    const int64_t* starts;  // [gridDim.x + 1] block boundaries in units, balanced by cost (claimed
-                            // launches: [nchunks + 1] chunk boundaries)
+    const int64_t* starts;  // [gridDim.x + 1] block boundaries in units, balanced by cost
     unsigned long long* hist;
     const uint8_t* S;
-    int32_t nchunks;        // claimed launches only: chunks of the partition
-    int* counter;           // claimed launches only: chunks claimed so far (zero before the launch)
+    unsigned long long* ranges;  // stealing launches only: [gridDim.x] units (next << 32 | end) each block
+                                 // has left, set to its static run before the launch
 };
 
 // ---------------------------------------------------------------------------
@@ -130,6 +133,51 @@ __device__ __forceinline__ bool consumer_sync(uint64_t* bar, uint32_t& phase)
     const bool ok = mbar_wait(bar, phase);
     phase ^= 1u;
     return ok;
+}
+
+// Warp-collective (the producer warp): finds the block whose run has the most units left, takes the
+// upper half of that run with one compare-and-swap and makes it this block's run (`mine`).  The
+// victim's owner claims from the front of its run with an atomic add on the same word, so the two
+// never overlap: either the swap sees the owner's latest claim or it fails.  False when no run has
+// `min_left` units left, or after kStealTries lost races.
+__device__ bool steal_half(unsigned long long* ranges, unsigned long long* mine, int nblocks, int lane, int64_t min_left)
+{
+    for (int t = 0; t < kStealTries; ++t) {
+        int64_t best = 0;
+        int victim = -1;
+        for (int v = lane; v < nblocks; v += 32) {
+            const unsigned long long w = __ldcg(ranges + v);
+            const int64_t rem = (int64_t)(w & 0xffffffffull) - (int64_t)(w >> 32);
+            if (rem > best) {
+                best = rem;
+                victim = v;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int64_t ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int ov = __shfl_xor_sync(0xffffffffu, victim, o);
+            if (ob > best || (ob == best && ov > victim)) {
+                best = ob;
+                victim = ov;
+            }
+        }
+        if (best < min_left) return false;
+        int won = 0;
+        if (lane == 0) {
+            const unsigned long long w = __ldcg(ranges + victim);
+            const unsigned long long n = w >> 32, e = w & 0xffffffffull;
+            if (e > n && (int64_t)(e - n) >= min_left) {
+                const unsigned long long cut = n + (e - n + 1) / 2;  // the owner keeps [n, cut)
+                if (atomicCAS(ranges + victim, w, (n << 32) | cut) == w) {
+                    atomicExch(mine, (cut << 32) | e);
+                    won = 1;
+                }
+            }
+        }
+        if (__shfl_sync(0xffffffffu, won, 0)) return true;
+    }
+    return false;
 }
 
 // ---------------------------------------------------------------------------
@@ -263,10 +311,12 @@ __device__ __forceinline__ BandCoef coef_of(const Args& a, const JobDesc* J, int
 // One persistent kernel for both passes (MODE) and both launch kinds (kBatch).
 // The launch's work is the concatenation over its jobs of (band, strip, row)
 // units; block k takes units [k q, (k + 1) q) and walks them tile by tile.
-// kClaim (batch pass 1 of the small tables only): instead of one precomputed run, a block claims
-// chunks of the partition from a.counter until none is left, so that blocks that finish early take
-// more; each ring stage carries its tile's chunk id (-1 ends the walk).
-template <int TC, int MODE, bool kBatch, class Args, bool kClaim = false>
+// kSteal (batch pass 1): a block starts on its static run as above, but claims it a granule at a
+// time from a.ranges[block], and once it is used up takes the upper half of the largest run left
+// (steal_half), so that blocks whose rows cost more than the plan priced them are helped by the
+// others; the runs stay contiguous, so a block rarely changes band (each change flushes its shared
+// histogram).  Each ring stage carries its tile's first unit and row count (unit -1 ends the walk).
+template <int TC, int MODE, bool kBatch, class Args, bool kSteal = false>
 __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant__ Args a)
 {
     constexpr int SW = 8 * TC;                 // strip width (columns)
@@ -299,8 +349,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
 
     // This block's share of the units, walked without divisions after the first.
     int64_t u0, u1;
-    if constexpr (kClaim) {
-        u0 = 0;  // the chunks are claimed below
+    if constexpr (kSteal) {
+        u0 = 0;  // claimed below
         u1 = 1;
     } else if constexpr (kBatch) {
         u0 = a.starts[blockIdx.x];
@@ -310,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
         u1 = min(a.units, u0 + a.units_per_block);
     }
     if (u0 >= u1) return;
-    int64_t left = kClaim ? 0 : u1 - u0;
+    int64_t left = kSteal ? 0 : u1 - u0;
     int j = 0;
     const JobDesc* Jp = job_ptr<kBatch>(a, 0);
     int H = 0, row = 0, band = 0, strip = 0;
@@ -333,34 +383,53 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
         band = (int)(seg / strips);
         strip = (int)(seg - (int64_t)band * strips);
     };
-    if constexpr (!kClaim) seek(u0);
-    int* stage_chunk = reinterpret_cast<int*>(csync + 1);  // claimed launches: each stage's chunk id
+    if constexpr (!kSteal) seek(u0);
+    // stealing launches: each stage's first unit (-1: the walk is over) and row count
+    int64_t* stage_unit = reinterpret_cast<int64_t*>(csync + 1);
+    int* stage_rows = reinterpret_cast<int*>(stage_unit + kStages);
     int stage = 0;
     uint32_t phase = 0;
 
     if (tid >= kConsumers) {
         // ------------------------------------------------------------ producer
-        if (tid != kConsumers) return;
+        if (!kSteal && tid != kConsumers) return;
         int issued = 0;
         bool ok = true;
-        if constexpr (kClaim) {
-            int c = atomicAdd(a.counter, 1);
-            while (ok && c < a.nchunks) {
-                const int64_t cu0 = a.starts[c], cu1 = a.starts[c + 1];
-                if (cu0 < cu1) {
-                    seek(cu0);
-                    tma_prefetch_map(map_of<kBatch>(a, j));
-                    int W = Jp->W;
-                    left = cu1 - cu0;
+        if constexpr (kSteal) {
+            // the whole producer warp looks for runs to steal; its lane 0 claims, issues and publishes
+            const int plane = tid - kConsumers;
+            unsigned long long* mine = a.ranges + blockIdx.x;
+            constexpr int64_t G = (int64_t)kStealGranule * RT;  // units per claim
+            int64_t next_unit = -1;  // lane 0: the unit after the last tile issued
+            int W = 0;
+            for (;;) {
+                unsigned long long old = 0;
+                if (plane == 0) old = atomicAdd(mine, (unsigned long long)G << 32);
+                old = __shfl_sync(0xffffffffu, old, 0);
+                const int64_t n0 = (int64_t)(old >> 32), e0 = (int64_t)(old & 0xffffffffull);
+                if (n0 >= e0) {
+                    if (!steal_half(a.ranges, mine, (int)gridDim.x, plane, 2 * G)) break;
+                    continue;
+                }
+                int good = 1;
+                if (plane == 0) {
+                    if (n0 != next_unit) {
+                        seek(n0);
+                        tma_prefetch_map(map_of<kBatch>(a, j));
+                        W = Jp->W;
+                    }
+                    int64_t u = n0;
+                    left = min(n0 + G, e0) - n0;
                     while (left > 0) {
                         const int nrows = (int)min((int64_t)min(RT, H - row), left);
                         if (issued >= kStages && !mbar_wait(&empty[stage], phase ^ 1u)) {
-                            ok = false;
+                            good = 0;
                             break;
                         }
                         const int x0 = strip * SW;
                         const int nb = min(NB, (W - x0 + 255) >> 8);
-                        stage_chunk[stage] = c;  // published by the arrive below
+                        stage_unit[stage] = u;  // published by the arrive below
+                        stage_rows[stage] = nrows;
                         mbar_arrive_expect_tx(&full[stage], (uint32_t)(nb * 512 * RT));
                         unsigned char* dst = ring + stage * kTileBytes;
                         const int y = band * H + row;
@@ -369,6 +438,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
                             tma_load_2d(dst + b * (RT * 512), map, &full[stage], x0 + b * 256, y);
                         ++issued;
                         left -= nrows;
+                        u += nrows;
                         row += nrows;
                         if (row == H) {
                             row = 0;
@@ -376,7 +446,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
                                 strip = 0;
                                 if (++band == Jp->bands) {
                                     band = 0;
-                                    if (left > 0) {
+                                    // the walk stands at the next job even when this claim ends here:
+                                    // the next claim may continue right there without a seek
+                                    if (j + 1 < a.njobs) {
                                         Jp = job_ptr<kBatch>(a, ++j);
                                         tma_prefetch_map(map_of<kBatch>(a, j));
                                         H = Jp->H;
@@ -387,15 +459,20 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
                         }
                         if (++stage == kStages) { stage = 0; phase ^= 1u; }
                     }
+                    next_unit = u;
                 }
-                if (ok) c = atomicAdd(a.counter, 1);
+                if (!__shfl_sync(0xffffffffu, good, 0)) {
+                    ok = false;
+                    break;
+                }
             }
+            if (plane != 0) return;
             if (ok) {
-                // the end of the walk: a stage without a copy, chunk -1
+                // the end of the walk: a stage without a copy, unit -1
                 if (issued >= kStages && !mbar_wait(&empty[stage], phase ^ 1u)) {
                     ok = false;
                 } else {
-                    stage_chunk[stage] = -1;
+                    stage_unit[stage] = -1;
                     mbar_arrive(&full[stage]);
                 }
             }
@@ -467,27 +544,28 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
     uint8_t* orow = nullptr;  // output passes: this thread's first byte of row (row + ph) of the segment
     int64_t opitch = 0;
     int vout = 0;
-    int cur_c = -1;    // claimed launches: the chunk being walked
-    int tab_key = -1;  // claimed launches: (job << 8) | band of the histogram held
+    int64_t expect = -1;  // stealing launches: the unit the walk stands at
+    int tab_key = -1;     // stealing launches: (job << 8) | band of the histogram held
     for (;;) {
-        if constexpr (kClaim) {
+        int nrows;
+        if constexpr (kSteal) {
             if (!mbar_wait(&full[stage], phase)) return;
-            const int c = stage_chunk[stage];
-            if (c < 0) break;  // the walk is over
-            if (c != cur_c) {
-                // the first tile of another chunk: it may start anywhere, in any band
-                cur_c = c;
-                seek(a.starts[c]);
-                left = a.starts[c + 1] - a.starts[c];
+            const int64_t u = stage_unit[stage];
+            if (u < 0) break;  // the walk is over
+            nrows = stage_rows[stage];
+            if (u != expect) {
+                // the first tile of a claim that does not continue the walk: any band of any job
+                seek(u);
                 new_seg = true;
             }
+            expect = u + nrows;
         } else {
             if (left <= 0) break;
+            nrows = (int)min((int64_t)min(RT, H - row), left);
         }
-        const int nrows = (int)min((int64_t)min(RT, H - row), left);
         if (new_seg) {
             bool new_band;  // a new band (of this or another job) starts
-            if constexpr (kClaim) new_band = ((j << 8) | band) != tab_key;
+            if constexpr (kSteal) new_band = ((j << 8) | band) != tab_key;
             else new_band = strip == 0 || !have_band;
             if (new_band) {
                 if (MODE == kHist && have_band) {
@@ -515,7 +593,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
                     if (!consumer_sync(csync, sync_phase)) return;
                 }
                 have_band = true;
-                if constexpr (kClaim) tab_key = (j << 8) | band;
+                if constexpr (kSteal) tab_key = (j << 8) | band;
             }
             new_seg = false;
             c0 = strip * SW + ct * 8;
@@ -547,7 +625,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
             // per tile, and the ring only advances at its slowest warp's pace.
             masked = __any_sync(0xffffffffu, n > 0 && n < 8);
         }
-        if constexpr (!kClaim) {
+        if constexpr (!kSteal) {
             if (!mbar_wait(&full[stage], phase)) return;
         }
         const unsigned char* tile = my + stage * kTileBytes;
@@ -606,7 +684,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
                 strip = 0;
                 if (++band == Jp->bands) {
                     band = 0;
-                    if (kBatch && left > 0) {
+                    // (stealing: the next tile may not continue the walk, but a next job exists to
+                    // stand at; a discontinuity is re-sought at the next stage)
+                    bool next_job = left > 0;
+                    if constexpr (kSteal) next_job = j + 1 < a.njobs;
+                    if (kBatch && next_job) {
                         Jp = job_ptr<kBatch>(a, ++j);
                         H = Jp->H;
                     }
@@ -752,9 +834,9 @@ int launch_batch(BatchArgs& a, int tc, int grid, cudaStream_t st)
     }
 }
 
-// Pass 1 with chunks claimed at run time (a.counter, a.nchunks).
+// Pass 1 with work stealing (a.ranges).
 template <int TC>
-int launch_batch_claim_tc(BatchArgs& a, int grid, cudaStream_t st)
+int launch_batch_steal_tc(BatchArgs& a, int grid, cudaStream_t st)
 {
     auto k = k_tma_strip<TC, kHist, true, BatchArgs, true>;
     const size_t smem = (size_t)kTableOffset + table_bytes(kHist, a.max_bits);
@@ -765,12 +847,12 @@ int launch_batch_claim_tc(BatchArgs& a, int grid, cudaStream_t st)
     return cuda_status(cudaGetLastError());
 }
 
-int launch_batch_claim(BatchArgs& a, int tc, int grid, cudaStream_t st)
+int launch_batch_steal(BatchArgs& a, int tc, int grid, cudaStream_t st)
 {
     switch (tc) {
-    case 256: return launch_batch_claim_tc<256>(a, grid, st);
-    case 128: return launch_batch_claim_tc<128>(a, grid, st);
-    default: return launch_batch_claim_tc<64>(a, grid, st);
+    case 256: return launch_batch_steal_tc<256>(a, grid, st);
+    case 128: return launch_batch_steal_tc<128>(a, grid, st);
+    default: return launch_batch_steal_tc<64>(a, grid, st);
     }
 }
 
@@ -917,9 +999,8 @@ int tma_batch_pass(const BatchLaunch& b, int mode, int column_threads, int block
     a.starts = b.starts;
     a.hist = b.hist;
     a.S = b.S;
-    a.nchunks = b.nchunks;
-    a.counter = b.counter;
-    if (mode == kHist && b.counter) return launch_batch_claim(a, column_threads, b.grid, st);
+    a.ranges = b.ranges;
+    if (mode == kHist && b.ranges) return launch_batch_steal(a, column_threads, b.grid, st);
     switch (mode) {
     case kHist: return launch_batch<kHist>(a, column_threads, b.grid, st);
     case kApplyStretch: return launch_batch<kApplyStretch>(a, column_threads, b.grid, st);
