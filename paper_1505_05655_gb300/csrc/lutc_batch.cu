@@ -50,10 +50,10 @@ constexpr int kSmallBits = 12;
 // shared-memory ring dominates), so the overhead term is a full strip's width.
 constexpr int kMaxGrid = 2048;  // blocks of a launch
 constexpr int kLaunches = 4;  // pass 1 (small tables), pass 1 (large tables), pass 2, detector only
-// Pass 1's launches steal work (measured: with one precomputed run per block the SMs of the small
-// tables' launch sat 20 % idle -- a model cannot price every image of a mix); each needs its blocks'
-// initial runs and the live copy the blocks claim from, kMaxGrid packed words each.
-constexpr int kStealLaunches = 2;
+// Pass 1's launches and pass 2 steal work (measured: with one precomputed run per block the SMs of
+// the small tables' pass 1 sat 20 % idle -- a model cannot price every image of a mix); each needs
+// its blocks' initial runs and the live copy the blocks claim from, kMaxGrid packed words each.
+constexpr int kStealLaunches = 3;
 constexpr int64_t kRowOverhead = 2048;
 
 void partition(const JobDesc* J, int n, int SW, int grid, int64_t* starts)
@@ -253,8 +253,8 @@ int enqueue(lutc_batch b, cudaStream_t st, cudaEvent_t* tr)
         L2.units = b->s_units - b->s_units_small;
         L2.starts = part + (kMaxGrid + 1);
         L2.grid = b->grid[1];
-        BatchLaunch* P1[kStealLaunches] = {&L1, &L2};
-        for (int l = 0; l < kStealLaunches; ++l) {
+        BatchLaunch* P1[2] = {&L1, &L2};
+        for (int l = 0; l < 2; ++l) {
             BatchLaunch& Lp = *P1[l];
             if (Lp.njobs <= 0) continue;
             if (b->steal) {
@@ -274,6 +274,13 @@ int enqueue(lutc_batch b, cudaStream_t st, cudaEvent_t* tr)
         if (tr) cudaEventRecord(tr[2], st);
         L.starts = part + 2 * (kMaxGrid + 1);
         L.grid = b->grid[2];
+        if (b->steal) {
+            uint64_t* init = steal + (size_t)2 * 2 * kMaxGrid;
+            L.ranges = reinterpret_cast<unsigned long long*>(init + kMaxGrid);
+            if ((rc = cuda_status(cudaMemcpyAsync(L.ranges, init, sizeof(uint64_t) * L.grid, cudaMemcpyDeviceToDevice,
+                                                  st))))
+                return rc;
+        }
         if ((rc = tma_batch_pass(L, kModeApplyStretch, tc, bps, st))) return rc;
     } else if (tr) {
         cudaEventRecord(tr[1], st);

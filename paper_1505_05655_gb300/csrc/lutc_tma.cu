@@ -834,12 +834,12 @@ int launch_batch(BatchArgs& a, int tc, int grid, cudaStream_t st)
     }
 }
 
-// Pass 1 with work stealing (a.ranges).
-template <int TC>
+// Launches with work stealing (a.ranges): pass 1 and pass 2 of a batch.
+template <int TC, int MODE>
 int launch_batch_steal_tc(BatchArgs& a, int grid, cudaStream_t st)
 {
-    auto k = k_tma_strip<TC, kHist, true, BatchArgs, true>;
-    const size_t smem = (size_t)kTableOffset + table_bytes(kHist, a.max_bits);
+    auto k = k_tma_strip<TC, MODE, true, BatchArgs, true>;
+    const size_t smem = (size_t)kTableOffset + table_bytes(MODE, a.max_bits);
     int64_t g = 0;
     int rc = grid_for(k, smem, 0, &g);  // raises the shared-memory limit on first use
     if (rc) return rc;
@@ -847,12 +847,13 @@ int launch_batch_steal_tc(BatchArgs& a, int grid, cudaStream_t st)
     return cuda_status(cudaGetLastError());
 }
 
+template <int MODE>
 int launch_batch_steal(BatchArgs& a, int tc, int grid, cudaStream_t st)
 {
     switch (tc) {
-    case 256: return launch_batch_steal_tc<256>(a, grid, st);
-    case 128: return launch_batch_steal_tc<128>(a, grid, st);
-    default: return launch_batch_steal_tc<64>(a, grid, st);
+    case 256: return launch_batch_steal_tc<256, MODE>(a, grid, st);
+    case 128: return launch_batch_steal_tc<128, MODE>(a, grid, st);
+    default: return launch_batch_steal_tc<64, MODE>(a, grid, st);
     }
 }
 
@@ -880,6 +881,7 @@ int preload_tc()
         if (!rc) rc = grid_for(k_tma_strip<TC, kHist, true, BatchArgs, true>, h, 0, &g);
         if (!rc) rc = grid_for(k_tma_strip<TC, kApplyStretch, false, TmaArgs>, t, 0, &g);
         if (!rc) rc = grid_for(k_tma_strip<TC, kApplyStretch, true, BatchArgs>, t, 0, &g);
+        if (!rc) rc = grid_for(k_tma_strip<TC, kApplyStretch, true, BatchArgs, true>, t, 0, &g);
         if (!rc) rc = grid_for(k_tma_strip<TC, kApplyDetector, false, TmaArgs>, z, 0, &g);
         if (!rc) rc = grid_for(k_tma_strip<TC, kApplyDetector, true, BatchArgs>, z, 0, &g);
     }
@@ -1000,7 +1002,8 @@ int tma_batch_pass(const BatchLaunch& b, int mode, int column_threads, int block
     a.hist = b.hist;
     a.S = b.S;
     a.ranges = b.ranges;
-    if (mode == kHist && b.ranges) return launch_batch_steal(a, column_threads, b.grid, st);
+    if (b.ranges && mode == kHist) return launch_batch_steal<kHist>(a, column_threads, b.grid, st);
+    if (b.ranges && mode == kApplyStretch) return launch_batch_steal<kApplyStretch>(a, column_threads, b.grid, st);
     switch (mode) {
     case kHist: return launch_batch<kHist>(a, column_threads, b.grid, st);
     case kApplyStretch: return launch_batch<kApplyStretch>(a, column_threads, b.grid, st);
