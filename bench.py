@@ -463,6 +463,9 @@ def run_lutc(args, wl):
     if wl.stretch and not args.no_plain:
         line["plain"] = run_plain(lutc, raw, dA, dG, dO, wl, device, stream, steps=max(3, min(args.steps, 20)))
 
+    if args.no_e2e:
+        del raw, out, wsb
+        return finish_lutc(args, line, wl, rank, ws, raw_h, out_h, A, G, O, value)
     # end to end through the C ABI with HOST buffers: lutc_correct_image_host pipelines the pinned
     # host raster in, both passes and the result out (chunks of rows, copy engines both ways)
     e2e_steps = max(3, min(args.steps, 10))
@@ -543,17 +546,28 @@ def run_lutc(args, wl):
                                      "samples_gpx_s": [round(wl.pixels * ws * e2e_steps / (t * 1e-3) / 1e9, 1)
                                                        for t in samples["copies"]]}}
 
+    # the device buffers of this leg are not needed by what follows (large14, the batch)
+    del raw, out, wsb, hws, fws, outs_h
+    gc.collect()
+    torch.cuda.empty_cache()
+    return finish_lutc(args, line, wl, rank, ws, raw_h, out_h, A, G, O, value)
+
+
+def finish_lutc(args, line, wl, rank, ws, raw_h, out_h, A, G, O, value):
+    """Oracle parity and CPU baseline, the sub-objects of the default line, and the line itself."""
+    import torch
+    import torch.distributed as dist
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], line["parity"] = cpu_baseline(wl, raw_h.numpy(), A, G, O, out_h.numpy())
     if ws > 1:
         dist.destroy_process_group()
-    if rank == 0 and ws == 1 and wl.name == "scene" and not args.quick:
+    if rank == 0 and ws == 1 and wl.name == "scene" and not args.quick and not (args.height or args.width):
         # the metric also names the batched and the served paths: summaries of both
         import copy
         sub = copy.copy(args)
         sub._return = True
         sub.steps, sub.warmup, sub.no_tune, sub.batch_images = 20, 3, False, 256
-        del raw, out, raw_h, out_h
+        del raw_h, out_h
         gc.collect()
         torch.cuda.empty_cache()
         # the large 14-bit scene on the same kernels, timed and checked against the oracle in full
@@ -565,7 +579,8 @@ def run_lutc(args, wl):
                            "images": b["config"]["images"], "pixels_per_step": b["config"]["pixels_per_step"],
                            "hbm_frac_step": b["hbm_frac_step"], "vs_fused_single": b["value"] / value,
                            "sequential_calls": b["sequential_calls"]["value"], "autotuned": b["config"]["autotuned"],
-                           "parity": b.get("parity"), "phases_ms": b["phases_ms"]}
+                           "parity": b.get("parity"), "phases_ms": b["phases_ms"], "roofline": b["roofline"],
+                           "clocks": b["clocks"], "cpu_baseline": b.get("cpu_baseline")}
         gc.collect()
         torch.cuda.empty_cache()
         v = serve_in_child(args)
@@ -826,21 +841,33 @@ def run_batch(args):
                     "d2h_bytes_per_step": sum(h.numel() for h in out_host), "steps": 3}}
     tr = line["roofline"]["traffic"]
     line["roofline"]["traffic_GBs"] = tr / (avg[dom] * 1e-3) / 1e9 if tr else None
+    n_sm = torch.cuda.get_device_properties(device).multi_processor_count
+    key = "batch" if align == 16 else "batch/align%d" % align
+    mhz = clocks["sm_mhz"] if clocks else None
+    line["roofline"]["smem_pipe"] = {"pass1": smem_pipe(key, "pass1", pixels, avg[0], mhz, n_sm),
+                                     "pass2": smem_pipe(key, "pass2", pixels, avg[2], mhz, n_sm)}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        sample = list(range(0, len(ims), 16))
-        t = time.perf_counter()
-        same = True
-        px = 0
-        for i in sample:
+        # every image against the oracle, one image per host thread at a time
+        import concurrent.futures as cf
+        threads = max(1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1))
+        got = [t[5].cpu().numpy() for t in images]
+
+        def same_as_oracle(i):
             im = ims[i]
             ref = oracle.correct_image(im["raw"][:, :, :im["width"]], im["A"], im["G"], im["O"], im["bits"])
-            px += ref.size
-            same = same and bool(np.array_equal(ref, images[i][5].cpu().numpy()))
+            return bool(np.array_equal(ref, got[i])), ref.size
+
+        t = time.perf_counter()
+        with cf.ThreadPoolExecutor(threads) as ex:
+            res = list(ex.map(same_as_oracle, range(len(ims))))
         dt = time.perf_counter() - t
-        line["cpu_baseline"] = {"value": px / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "images %s of the batch (%d px), single-threaded C oracle, %.1f s"
-                                          % (",".join(map(str, sample)), px, dt)}
-        line["parity"] = {"bit_exact_vs_oracle": same, "pixels_compared": px}
+        px = sum(n for _, n in res)
+        line["cpu_baseline"] = {"value": px / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": "every image of the batch (%d px), the oracle's correct_image, one image "
+                                          "per thread on %d threads, %.1f s" % (px, threads, dt)}
+        line["parity"] = {"bit_exact_vs_oracle": all(ok for ok, _ in res), "pixels_compared": px,
+                          "images_compared": len(res)}
+        del got
     batch.close()
     if getattr(args, "_return", False):
         return line
@@ -932,7 +959,7 @@ def run_serve(args):
     for rate, n in ((50, max(2000, args.steps // 4)), (200, max(2000, args.steps)), (800, max(2000, 2 * args.steps))):
         loads[str(rate)] = drive(rate, n)
     # loads high enough to batch for real: fractions of the saturated request rate, ~1 s each
-    for frac in (0.25, 0.5, 0.75):
+    for frac in (0.25, 0.5, 0.75, 0.9):
         rate = frac * sat["req_s"]
         loads["%d%% of saturation" % round(100 * frac)] = drive(rate, int(max(2000, min(60000, rate))))
     # requests from pinned host memory: staged in and out by the server (copies inside each request's latency)
@@ -960,7 +987,7 @@ def run_serve(args):
             "warmup": warm["requests"], "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": "serve: %d sensors from the batch mixture, %d pool rasters each, device-resident; "
-                                   "Poisson arrivals 50/200/800 req/s and 25/50/75 %% of the saturated request "
+                                   "Poisson arrivals 50/200/800 req/s and 25/50/75/90 %% of the saturated request "
                                    "rate; budget 40 GiB; a request launches at once on an idle device, else batches "
                                    "<= 32 requests or 2 ms, 4 streams" % (nsens, pool_per_sensor),
                        "row_align_bytes": args.row_align, "mean_request_px": mean_px,
@@ -1217,6 +1244,10 @@ def main():
     ap.add_argument("--row-align", type=int, default=128, choices=[16, 32, 64, 128, 256, 512],
                     help="batch and serve workloads: bytes every image row is padded to (input and output)")
     ap.add_argument("--quick", action="store_true", help="scene line only (no batch and serving summaries)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) leg")
+    ap.add_argument("--height", type=int, default=0, help="single-image workloads: rows per band instead of the "
+                                                          "workload's (a smaller case of it, e.g. for a profile)")
+    ap.add_argument("--width", type=int, default=0, help="single-image workloads: columns instead of the workload's")
     ap.add_argument("--cases", default="", help="fit / demosaic workloads: run only the cases whose name contains "
                                                   "one of these comma-separated words ('_' stands for a space)")
     args = ap.parse_args()
@@ -1233,6 +1264,9 @@ def main():
         print(json.dumps({"workload": "fit", "fit": run_fit(args)}), flush=True)
         return
     wl = synth.WORKLOADS[args.workload if args.workload in synth.WORKLOADS else "scene"]
+    if args.height or args.width:
+        import dataclasses
+        wl = dataclasses.replace(wl, height=args.height or wl.height, width=args.width or wl.width)
     if args.impl == "reference":
         run_reference(args, wl)
     else:
