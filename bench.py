@@ -54,6 +54,7 @@ def peaks():
 # sources whose change invalidates a committed DRAM-traffic figure, per workload
 TRAFFIC_SOURCES = {
     "scene": ["csrc/lutc_tma.cu", "csrc/lutc_ptx.cuh", "csrc/lutc_internal.cuh", "csrc/lutc_correct.cu", "_build.py"],
+    "large14": ["csrc/lutc_tma.cu", "csrc/lutc_ptx.cuh", "csrc/lutc_internal.cuh", "csrc/lutc_correct.cu", "_build.py"],
     "batch": ["csrc/lutc_tma.cu", "csrc/lutc_ptx.cuh", "csrc/lutc_internal.cuh", "csrc/lutc_batch.cu", "_build.py"],
 }
 

@@ -200,7 +200,8 @@ struct lutc_batch_st {
     int64_t s_units_small = 0;  // units of the first ns_small stretch jobs
     int small_max_bits = 8;
     int grid[kLaunches] = {0, 0, 0, 0};
-    bool steal = false;  // pass 1 steals work (unit numbers fit the packed runs)
+    bool steal = false;  // pass 1 and pass 2 steal work (unit numbers fit the packed runs)
+    int granule[kLaunches] = {0, 0, 0, 0};  // units per claim of each stealing launch
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -261,6 +262,7 @@ int enqueue(lutc_batch b, cudaStream_t st, cudaEvent_t* tr)
                 // every run back at its planned start (the previous run left them used up)
                 uint64_t* init = steal + (size_t)l * 2 * kMaxGrid;
                 Lp.ranges = reinterpret_cast<unsigned long long*>(init + kMaxGrid);
+                Lp.granule = b->granule[l];
                 if ((rc = cuda_status(cudaMemcpyAsync(Lp.ranges, init, sizeof(uint64_t) * Lp.grid,
                                                       cudaMemcpyDeviceToDevice, st))))
                     return rc;
@@ -277,6 +279,7 @@ int enqueue(lutc_batch b, cudaStream_t st, cudaEvent_t* tr)
         if (b->steal) {
             uint64_t* init = steal + (size_t)2 * 2 * kMaxGrid;
             L.ranges = reinterpret_cast<unsigned long long*>(init + kMaxGrid);
+            L.granule = b->granule[2];
             if ((rc = cuda_status(cudaMemcpyAsync(L.ranges, init, sizeof(uint64_t) * L.grid, cudaMemcpyDeviceToDevice,
                                                   st))))
                 return rc;
@@ -450,13 +453,19 @@ extern "C" int lutc_batch_create(const lutc_job* jobs, int n, const lutc_batch_c
             b->grid[l] = g;
             partition(L[l].J, L[l].n, SW, std::max(g, 1), part + (size_t)l * (kMaxGrid + 1));
         }
-        // pass 1's initial runs as packed (start << 32 | end) words, when every unit number fits
+        // the stealing launches' initial runs as packed (start << 32 | end) words, when every unit number
+        // fits, and their claim size: about a sixteenth of a block's share in whole tiles, one to eight
+        // (a claim costs one atomic round trip; the last claims set how evenly the blocks finish)
         b->steal = b->s_units < kStealMaxUnits;
         uint64_t* steal = reinterpret_cast<uint64_t*>(b->blob.data() + p.off_steal);
+        const int64_t units_of[kStealLaunches] = {b->s_units_small, b->s_units - b->s_units_small, b->s_units};
+        const int64_t rt = tma_box_rows(tc);
         for (int l = 0; l < kStealLaunches && b->steal; ++l) {
             const int64_t* st0 = part + (size_t)l * (kMaxGrid + 1);
             for (int k = 0; k < b->grid[l]; ++k)
                 steal[(size_t)l * 2 * kMaxGrid + k] = ((uint64_t)st0[k] << 32) | (uint64_t)st0[k + 1];
+            const int64_t per_block = b->grid[l] > 0 ? units_of[l] / b->grid[l] : 0;
+            b->granule[l] = (int)(rt * std::min<int64_t>(8, std::max<int64_t>(1, per_block / (16 * rt))));
         }
     }
     if (p.off_hist > 0) {

@@ -110,6 +110,7 @@ struct BatchLaunch {
     unsigned long long* ranges = nullptr;  // pass 1 only: [grid] packed (next << 32 | end) runs the blocks
                               // claim from and steal from, set to starts[] before the launch (or nullptr:
                               // static runs)
+    int32_t granule = 0;      // units per claim of a stealing launch (0: eight tiles)
     int32_t grid;
     unsigned long long* hist;
     const uint8_t* S;

@@ -70,9 +70,9 @@ constexpr int kRingBytes = kStages * kTileBytes;
 constexpr int kBarRegion = ((2 * kStages + 1) * 8 + 127) / 128 * 128;
 constexpr int kTableOffset = kRingBytes + kBarRegion;
 static_assert((2 * kStages + 1) * 8 + kStages * 12 <= kBarRegion, "barrier region (barriers, per-stage tile units)");
-// Work stealing (batch pass 1): a block claims kStealGranule tiles' worth of units of its own run at a
-// time, and a run with fewer than two granules left is not stolen from.
-constexpr int kStealGranule = 8;
+// Work stealing (batch passes): a block claims a.granule units of its own run at a time (planned per
+// launch: about a sixteenth of a block's share, one to eight tiles), and a run with fewer than two
+// granules left is not stolen from.
 constexpr int kStealTries = 8;  // lost compare-and-swap races before a block stops looking for work
 static_assert(kTableOffset % 128 == 0, "table alignment");
 
@@ -107,6 +107,7 @@ struct BatchArgs {
     const uint8_t* S;
     unsigned long long* ranges;  // stealing launches only: [gridDim.x] units (next << 32 | end) each block
                                  // has left, set to its static run before the launch
+    int32_t granule;             // stealing launches only: units per claim (>= 1)
 };
 
 // ---------------------------------------------------------------------------
@@ -399,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
             // the whole producer warp looks for runs to steal; its lane 0 claims, issues and publishes
             const int plane = tid - kConsumers;
             unsigned long long* mine = a.ranges + blockIdx.x;
-            constexpr int64_t G = (int64_t)kStealGranule * RT;  // units per claim
+            const int64_t G = a.granule;  // units per claim
             int64_t next_unit = -1;  // lane 0: the unit after the last tile issued
             int W = 0;
             for (;;) {
@@ -1002,6 +1003,7 @@ int tma_batch_pass(const BatchLaunch& b, int mode, int column_threads, int block
     a.hist = b.hist;
     a.S = b.S;
     a.ranges = b.ranges;
+    a.granule = b.granule > 0 ? b.granule : 8 * tma_box_rows(column_threads);
     if (b.ranges && mode == kHist) return launch_batch_steal<kHist>(a, column_threads, b.grid, st);
     if (b.ranges && mode == kApplyStretch) return launch_batch_steal<kApplyStretch>(a, column_threads, b.grid, st);
     switch (mode) {
