@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(Tile<kCorrect>::threads, Tile<kCorrect>::min_b
 
 // ---------------------------------------------------------------------------
 // TMA-fed persistent version (frames with 16-byte aligned rows, at least one
-// staged tile in each direction).  A block keeps two 128 x 32 tiles (with
+// staged tile in each direction).  A block keeps two 128 x 64 tiles (with
 // their halo) in flight through cp.async.bulk.tensor loads into a 2-stage
 // ring (zeros outside the frame) while it computes the current one.  The
 // grid is one wave and the blocks sweep the frame together: at step k block
@@ -249,23 +249,41 @@ __global__ void __launch_bounds__(Tile<kCorrect>::threads, Tile<kCorrect>::min_b
 // where each block took its own contiguous run of tiles was slower than the
 // plain kernel, 580 against 474 us at 16384^2, and so was a grid of whole
 // blocks per column strip, which leaves SMs unevenly loaded: 465 us.)
-// With correction, the block corrects each staged tile in place before the
-// interpolation: a thread owns 4 staged columns (their coefficients read
-// per tile) and a seventh of the rows.
+// With correction, the block corrects the staged tile in place before the
+// interpolation: a thread owns 4 staged columns (their coefficients staged
+// with the tile) and a seventh of the rows.  Only the 136 staged columns the
+// interpolation reads are corrected (the 8-column alignment halo holds 7
+// unused columns on each side); a tile of 64 rows keeps the corrected halo
+// rows at 2 in 66, so step L runs 1.10 times per output pixel.
 // ---------------------------------------------------------------------------
-constexpr int kQW = 128, kQH = 32, kQSW = kQW + 16, kQSH = kQH + 2, kQThreads = (kQW / 8) * (kQH / 2);
+constexpr int kQW = 128, kQSW = kQW + 16;
+constexpr int kQPatchRows = 32;                             // rows one pass of the block's 2 x 8 patches covers
+constexpr int kQThreads = (kQW / 8) * (kQPatchRows / 2);
 constexpr int kQStages = 2;
-constexpr int kQStageElems = (kQSW * kQSH + 63) / 64 * 64;  // stages 128-byte aligned
-constexpr uint32_t kQBoxBytes = kQSW * kQSH * 2;
-constexpr int kQLanes = kQThreads / (kQSW / 4);             // correction: row lanes of 36 x 4 columns
+// Tile height: 64 rows halve the corrected halo rows (2 in 66), 32 rows keep the raw sweep's DRAM
+// locality (its blocks then cover half as many rows at a time) and give small frames more tiles.
+#ifndef LUTC_DEMOSAIC_CORRECTED_ROWS
+#define LUTC_DEMOSAIC_CORRECTED_ROWS 64
+#endif
+template <int kTH>
+struct QTile {
+    static constexpr int H = kTH, SH = kTH + 2;
+    static constexpr int StageElems = (kQSW * SH + 63) / 64 * 64;  // stages 128-byte aligned
+    static constexpr uint32_t BoxBytes = kQSW * SH * 2;
+    static_assert(H % kQPatchRows == 0 && SH <= 256 && (StageElems * 2) % 128 == 0, "tile geometry");
+};
+constexpr int kQQuad0 = 1, kQQuads = kQSW / 4 - 2;          // correction: staged column groups 1 .. 34
+constexpr int kQLanes = kQThreads / kQQuads;                // correction: row lanes
 // a staged coefficient row: kQSW int32 padded so that every row of every stage starts on the
 // 128-byte boundary a tiled tensor copy writes to
 constexpr int kQCoefRow = (kQSW * 4 + 127) / 128 * 128 / 4;
 static_assert(kQThreads == 256 && kQLanes >= 1, "tile geometry");
-static_assert((kQStageElems * 2) % 128 == 0 && (kQCoefRow * 4) % 128 == 0, "TMA destinations 128-byte aligned");
+static_assert(kQQuad0 * 4 + 3 >= 7 && (kQQuad0 + kQQuads) * 4 <= kQSW && (kQQuad0 + kQQuads) * 4 >= 8 + kQW + 1,
+              "the corrected groups cover staged columns 7 .. kQW + 8, all the interpolation reads");
+static_assert(kQSW <= 256 && (kQCoefRow * 4) % 128 == 0, "TMA box width, coefficient rows 128-byte aligned");
 
 struct DemosaicTmaArgs {
-    CUtensorMap map;      // uint16 [H][W], row stride = pitch, box {kQSW, kQSH}
+    CUtensorMap map;      // uint16 [H][W], row stride = pitch, box {kQSW, tile rows + 2}
     CUtensorMap cmap[3];  // int32 [W] coefficient rows A, G, O, box {kQSW} (when coef_tma)
     int W, H, bits;
     BandCoef coef;        // A == nullptr: no correction
@@ -302,10 +320,12 @@ struct TileCursor {
     }
 };
 
-template <int PY, int PX, bool kCorrect>
+template <int PY, int PX, bool kCorrect, int kTH>
 __global__ void __launch_bounds__(kQThreads, 3) k_demosaic_tma(const __grid_constant__ DemosaicTmaArgs a)
 {
-    __shared__ __align__(128) uint16_t ring[kQStages][kQStageElems];
+    using Q = QTile<kTH>;
+    constexpr int kQH = Q::H, kQSH = Q::SH;
+    __shared__ __align__(128) uint16_t ring[kQStages][Q::StageElems];
     __shared__ __align__(128) int32_t cbuf[kCorrect ? kQStages : 1][3][kCorrect ? kQCoefRow : 4];
     __shared__ __align__(8) uint64_t full[kQStages];
     const int tid = threadIdx.x;
@@ -330,7 +350,7 @@ __global__ void __launch_bounds__(kQThreads, 3) k_demosaic_tma(const __grid_cons
         const int s = (int)(k % kQStages);
         uint64_t* bar = &full[s];
         const int x = icur.tx * kQW - 8;  // a multiple of 8 columns: 16-byte aligned for both maps
-        ptx::mbar_arrive_expect_tx(bar, kQBoxBytes + (ctma ? 3u * kQSW * 4u : 0u));
+        ptx::mbar_arrive_expect_tx(bar, Q::BoxBytes + (ctma ? 3u * kQSW * 4u : 0u));
         ptx::tma_load_2d(ring[s], &a.map, bar, x, icur.ty * kQH - 1);
         if (kCorrect && ctma)
             for (int c = 0; c < 3; ++c) ptx::tma_load_1d(cbuf[s][c], &a.cmap[c], bar, x);
@@ -341,7 +361,8 @@ __global__ void __launch_bounds__(kQThreads, 3) k_demosaic_tma(const __grid_cons
 
     const int32_t M = (1 << a.bits) - 1;
     const uint32_t M2 = (uint32_t)M | ((uint32_t)M << 16);
-    const int q = tid % (kQSW / 4), lane = tid / (kQSW / 4);
+    const bool packed = a.bits <= 15;  // clamps two DN per instruction as signed 16-bit halves
+    const int q = kQQuad0 + tid % kQQuads, lane = tid / kQQuads;
     int64_t k = 0;
     for (; k < n; ++k, cur.next()) {
         const int s = (int)(k % kQStages);
@@ -378,30 +399,45 @@ __global__ void __launch_bounds__(kQThreads, 3) k_demosaic_tma(const __grid_cons
                     fits[j] = col_fits_i32(cA[j], cG[j], cO[j], M);
                     if (fits[j]) cO[j] += 32768;
                 }
-                // rows of the frame only (zeros from the load stay zeros)
-                const int r_lo = max(lane, lane + (1 - y0 + kQLanes - 1 - lane) / kQLanes * kQLanes);
+                // rows of the frame only (zeros from the load stay zeros): staged row 0 is frame row
+                // y0 - 1, outside the frame on the top tile row
+                const int r_lo = (y0 == 0 && lane == 0) ? kQLanes : lane;
                 const int r_hi = min(kQSH, a.H - y0 + 1);
                 const int gx0 = x0 - 8 + q * 4;
                 if (gx0 >= 0 && gx0 + 4 <= a.W && fits[0] && fits[1] && fits[2] && fits[3]) {
-                    // the common case: four columns inside the frame, all int32-exact; two rows per
-                    // step, so eight independent evaluations are in flight
+                    // the common case: four columns inside the frame, all int32-exact
+                    auto pair = [&](uint32_t w, int j) {  // columns j, j + 1 of the thread's four
+                        w = __vminu2(w, M2);  // both raw DN clamped to M at once
+                        const uint32_t xa = w & 0xffffu, xb = w >> 16;
+                        if (packed) {
+                            // floor(t / 2^16) of an exact int32 t is its high half read as a signed
+                            // 16-bit value: gather both high halves, clamp both to [0, M] at once
+                            const uint32_t ta = ((uint32_t)cA[j] * xa + (uint32_t)cG[j]) * xa + (uint32_t)cO[j];
+                            const uint32_t tb = ((uint32_t)cA[j + 1] * xb + (uint32_t)cG[j + 1]) * xb +
+                                                (uint32_t)cO[j + 1];
+                            return __vimin_s16x2_relu(__byte_perm(ta, tb, 0x7632), M2);
+                        }
+                        return det_i32(cA[j], cG[j], cO[j], xa, M) | (det_i32(cA[j + 1], cG[j + 1], cO[j + 1], xb, M) << 16);
+                    };
                     auto correct4 = [&](uint2 w) {
-                        w.x = __vminu2(w.x, M2);  // both halves clamped to M at once
-                        w.y = __vminu2(w.y, M2);
-                        const uint32_t x0v = w.x & 0xffffu, x1v = w.x >> 16, x2v = w.y & 0xffffu, x3v = w.y >> 16;
-                        w.x = det_i32(cA[0], cG[0], cO[0], x0v, M) | (det_i32(cA[1], cG[1], cO[1], x1v, M) << 16);
-                        w.y = det_i32(cA[2], cG[2], cO[2], x2v, M) | (det_i32(cA[3], cG[3], cO[3], x3v, M) << 16);
+                        w.x = pair(w.x, 0);
+                        w.y = pair(w.y, 2);
                         return w;
                     };
+                    // four rows per step: sixteen independent evaluations in flight
                     int r = r_lo;
-                    for (; r + kQLanes < r_hi; r += 2 * kQLanes) {
-                        uint2* p0 = reinterpret_cast<uint2*>(&st[r][q * 4]);
-                        uint2* p1 = reinterpret_cast<uint2*>(&st[r + kQLanes][q * 4]);
-                        const uint2 w0 = *p0, w1 = *p1;
-                        *p0 = correct4(w0);
-                        *p1 = correct4(w1);
+                    for (; r + 3 * kQLanes < r_hi; r += 4 * kQLanes) {
+                        uint2* p[4];
+                        uint2 w[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            p[u] = reinterpret_cast<uint2*>(&st[r + u * kQLanes][q * 4]);
+                            w[u] = *p[u];
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) *p[u] = correct4(w[u]);
                     }
-                    if (r < r_hi) {
+                    for (; r < r_hi; r += kQLanes) {
                         uint2* p0 = reinterpret_cast<uint2*>(&st[r][q * 4]);
                         *p0 = correct4(*p0);
                     }
@@ -426,7 +462,11 @@ __global__ void __launch_bounds__(kQThreads, 3) k_demosaic_tma(const __grid_cons
             }
             __syncthreads();
         }
-        patch<PY, PX, kQW, kQH, kQSW>(st, x0, y0, a.W, a.H, a.out, a.out_pitch, a.vout != 0);
+        // one copy of the patch code for every 32-row part of the tile (unrolled, the interpolation's
+        // code twice over misses the instruction cache)
+#pragma unroll 1
+        for (int h = 0; h < kQH; h += kQPatchRows)
+            patch<PY, PX, kQW, kQPatchRows, kQSW>(st + h, x0, y0 + h, a.W, a.H, a.out, a.out_pitch, a.vout != 0);
         __syncthreads();  // every thread is done with stage s
         if (tid == 0 && k + kQStages < n) {
             ptx::fence_proxy_async_smem();  // this block's generic accesses to the stage come before the reload
@@ -440,30 +480,38 @@ __global__ void __launch_bounds__(kQThreads, 3) k_demosaic_tma(const __grid_cons
     }
 }
 
-template <bool kCorrect>
-int launch_tma(int py, int px, cudaStream_t st, DemosaicTmaArgs& a)
+// Blocks of the persistent TMA-fed grid: SMs x resident blocks (computed once per device and kernel kind).
+template <bool kCorrect, int kTH>
+int tma_blocks_per_sm()
 {
-    static int per_sm_cache[2][64] = {};
+    static int cache[64] = {};
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LUTC_ECUDA;
-    int& per_sm = per_sm_cache[kCorrect][dev];
-    if (per_sm == 0) {
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (cache[dev] == 0) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_demosaic_tma<0, 0, kCorrect>, kQThreads, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_demosaic_tma<0, 0, kCorrect, kTH>, kQThreads, 0) !=
                 cudaSuccess ||
             b < 1) {
             cudaGetLastError();
             b = 1;
         }
-        per_sm = b;
+        cache[dev] = b;
     }
+    return cache[dev];
+}
+
+template <bool kCorrect, int kTH>
+int launch_tma(int py, int px, cudaStream_t st, DemosaicTmaArgs& a)
+{
+    const int per_sm = tma_blocks_per_sm<kCorrect, kTH>();
+    if (per_sm < 1) return LUTC_ECUDA;
     // one wave, never more blocks than tiles
     const int64_t blocks = std::min<int64_t>(a.ntiles, (int64_t)sm_count() * per_sm);
     switch (2 * py + px) {
-    case 0: k_demosaic_tma<0, 0, kCorrect><<<(unsigned)blocks, kQThreads, 0, st>>>(a); break;
-    case 1: k_demosaic_tma<0, 1, kCorrect><<<(unsigned)blocks, kQThreads, 0, st>>>(a); break;
-    case 2: k_demosaic_tma<1, 0, kCorrect><<<(unsigned)blocks, kQThreads, 0, st>>>(a); break;
-    default: k_demosaic_tma<1, 1, kCorrect><<<(unsigned)blocks, kQThreads, 0, st>>>(a); break;
+    case 0: k_demosaic_tma<0, 0, kCorrect, kTH><<<(unsigned)blocks, kQThreads, 0, st>>>(a); break;
+    case 1: k_demosaic_tma<0, 1, kCorrect, kTH><<<(unsigned)blocks, kQThreads, 0, st>>>(a); break;
+    case 2: k_demosaic_tma<1, 0, kCorrect, kTH><<<(unsigned)blocks, kQThreads, 0, st>>>(a); break;
+    default: k_demosaic_tma<1, 1, kCorrect, kTH><<<(unsigned)blocks, kQThreads, 0, st>>>(a); break;
     }
     return cuda_status(cudaGetLastError());
 }
@@ -513,12 +561,19 @@ extern "C" int lutc_demosaic(const lutc_raster* in, const lutc_coeffs* coeffs, i
     cudaStream_t st = (cudaStream_t)stream;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     int* status = device_status_ptr();
+    // tile height: the taller tile for corrected frames with at least two tiles per block of one wave
+    constexpr int kTall = LUTC_DEMOSAIC_CORRECTED_ROWS, kShort = 32;
+    const int64_t strips = (in->width + kQW - 1) / kQW;
+    const bool tall = coeffs && kTall != kShort && in->height >= QTile<kTall>::SH &&
+                      strips * ((in->height + kTall - 1) / kTall) >=
+                          2 * (int64_t)sm_count() * std::max(1, tma_blocks_per_sm<true, kTall>());
+    const int th = tall ? kTall : kShort;
     if (enc && status && ((uintptr_t)in->data % 16) == 0 && (in->pitch_bytes % 16) == 0 && in->width >= kQSW &&
-        in->height >= kQSH) {
+        in->height >= th + 2) {
         DemosaicTmaArgs t;
         const cuuint64_t dims[2] = {(cuuint64_t)in->width, (cuuint64_t)in->height};
         const cuuint64_t strides[1] = {(cuuint64_t)in->pitch_bytes};
-        const cuuint32_t box[2] = {(cuuint32_t)kQSW, (cuuint32_t)kQSH};
+        const cuuint32_t box[2] = {(cuuint32_t)kQSW, (cuuint32_t)(th + 2)};
         const cuuint32_t estr[2] = {1, 1};
         if (enc(&t.map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<uint16_t*>(in->data), dims, strides, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -543,11 +598,12 @@ extern "C" int lutc_demosaic(const lutc_raster* in, const lutc_coeffs* coeffs, i
             t.out = a.out;
             t.out_pitch = a.out_pitch;
             t.vout = a.vout;
-            t.strips = (in->width + kQW - 1) / kQW;
-            t.ntiles = (int64_t)t.strips * ((in->height + kQH - 1) / kQH);
+            t.strips = (int)strips;
+            t.ntiles = strips * ((in->height + th - 1) / th);
             t.status = status;
-            return coeffs ? launch_tma<true>(kPY[pattern], kPX[pattern], st, t)
-                          : launch_tma<false>(kPY[pattern], kPX[pattern], st, t);
+            if (!coeffs) return launch_tma<false, kShort>(kPY[pattern], kPX[pattern], st, t);
+            return tall ? launch_tma<true, kTall>(kPY[pattern], kPX[pattern], st, t)
+                        : launch_tma<true, kShort>(kPY[pattern], kPX[pattern], st, t);
         }
     }
     if ((in->height + 15) / 16 > 65535) return LUTC_EUNSUPPORTED;  // grid rows of the raw path's 16-row tiles

@@ -1,7 +1,8 @@
 """Parity of the CUDA bilinear demosaic with the oracle (GPU).
 
-Integer arithmetic throughout: tolerance zero.  Shapes span several 128 x 32
-tiles with ragged right and bottom edges, tiles whose halo leaves the image,
+Integer arithmetic throughout: tolerance zero.  Shapes span several tiles
+(128 x 64 on the TMA-fed path, 128 x 16 or 128 x 32 on the plain one) with
+ragged right and bottom edges, tiles whose halo leaves the image,
 degenerate images one pixel wide or high, unaligned rows on both sides, coefficient
 rows off a 16-byte boundary (no TMA staging of the coefficients), all
 four CFA patterns, with and without the fused detector correction (int32 and
@@ -75,7 +76,7 @@ def test_fused_detector_correction(pattern, bits):
 
 # 16-byte aligned rows: the vector staging path, ragged in both directions, pitches padded to 16 bytes
 ALIGNED_SHAPES = [(67, 304, 0), (100, 1032, 0), (35, 144, 0), (34, 152, 0), (300, 1160, 0), (97, 300, 4), (259, 517, 3),
-              (1000, 2048, 0)]
+              (1000, 2048, 0), (66, 144, 0), (130, 152, 0)]
 
 
 @pytest.mark.parametrize("pattern", PATTERNS)
@@ -88,6 +89,19 @@ def test_aligned_rows_raw_and_corrected(pattern, h, w, pad):
     A[::29] = 900  # int64 columns
     np.testing.assert_array_equal(_gpu(img, w, pattern, bits), _ref(img, w, pattern, bits))
     np.testing.assert_array_equal(_gpu(img, w, pattern, bits, (A, G, O)), _ref(img, w, pattern, bits, (A, G, O)))
+
+
+@pytest.mark.parametrize("bits", [8, 10, 14, 15, 16])
+@pytest.mark.parametrize("h,w", [(66, 152), (129, 304), (197, 1032)])
+def test_aligned_rows_corrected_every_bit_depth(bits, h, w):
+    # the TMA-fed corrected path at every bit depth (two DN clamped per instruction up to 15 bits,
+    # one at 16) on frames of one, two and four 64-row tiles, ragged; int64 columns and DN above M
+    img = _raw(40 + bits + h, h, w, bits)
+    img[::9, ::11] = 65535
+    A, G, O = synth.coeffs(40 + bits, 0, w)
+    A[::31] = 900
+    for pattern in ("rggb", "grbg"):
+        np.testing.assert_array_equal(_gpu(img, w, pattern, bits, (A, G, O)), _ref(img, w, pattern, bits, (A, G, O)))
 
 
 @pytest.mark.parametrize("in_off,pad,out_pad", [(1, 3, 1), (3, 0, 5), (0, 8, 0), (5, 1, 3)])
