@@ -367,7 +367,7 @@ def fused_roofline(wl, workload: str, phases, path: int, clocks, peak: float, pe
     mhz = clocks["sm_mhz"] if clocks else None
     pipe = {k: smem_pipe(workload, k, wl.pixels, avg[i], mhz, sms) if tma else None
             for i, k in ((0, "pass1"), (2, "pass2"))}
-    tr = ncu_traffic(keys[dom], workload) if tma else None
+    tr = ncu_traffic(keys[dom], workload, wl.pixels) if tma else None
     roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "traffic": tr, "kernel": "%s %s" % (keys[dom], kern[dom]),
             "kernel_family": "tma" if tma else "strip (lutc_last_path)",
@@ -584,7 +584,7 @@ def finish_lutc(args, line, wl, rank, ws, raw_h, out_h, A, G, O, value):
                            "clocks": b["clocks"], "cpu_baseline": b.get("cpu_baseline")}
         gc.collect()
         torch.cuda.empty_cache()
-        v = serve_in_child(args)
+        v = serve_in_child(args, value)
         line["served"] = served_summary(v, value)
         line["fit"] = run_fit(sub)
         line["demosaic"] = run_demosaic(sub)
@@ -963,6 +963,10 @@ def run_serve(args):
     for frac in (0.25, 0.5, 0.75, 0.9):
         rate = frac * sat["req_s"]
         loads["%d%% of saturation" % round(100 * frac)] = drive(rate, int(max(2000, min(60000, rate))))
+    # the metric's own target: an offered load of 80 % of the fused single-scene rate, when it is known
+    if args.fused_gpx:
+        rate = 0.8 * args.fused_gpx * 1e9 / mean_px
+        loads["80% of the fused scene"] = drive(rate, int(max(2000, min(60000, rate))))
     # requests from pinned host memory: staged in and out by the server (copies inside each request's latency)
     host_sat = drive(0, max(300, args.steps), closed=True, host=True)
     host_200 = drive(200, max(300, args.steps // 2), host=True)
@@ -988,8 +992,8 @@ def run_serve(args):
             "warmup": warm["requests"], "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": "serve: %d sensors from the batch mixture, %d pool rasters each, device-resident; "
-                                   "Poisson arrivals 50/200/800 req/s and 25/50/75/90 %% of the saturated request "
-                                   "rate; budget 40 GiB; a request launches at once on an idle device, else batches "
+                                   "Poisson arrivals 50/200/800 req/s, 25/50/75/90 %% of the saturated request "
+                                   "rate and 80 %% of the fused single-scene rate; budget 40 GiB; a request launches at once on an idle device, else batches "
                                    "<= 32 requests or 2 ms, 4 streams" % (nsens, pool_per_sensor),
                        "row_align_bytes": args.row_align, "mean_request_px": mean_px,
                        "load_generator": "lutc_server_replay: arrival times drawn up front, submitted on schedule "
@@ -1006,11 +1010,11 @@ def run_serve(args):
         print(json.dumps(line), flush=True)
 
 
-def serve_in_child(args):
+def serve_in_child(args, fused_gpx: float | None = None):
     """The serving summary from a fresh process (`--workload serve`): its latency tails measure the
     server, not the many GB this process has allocated and freed by then."""
     cmd = [sys.executable, os.path.abspath(__file__), "--workload", "serve", "--steps", "1000",
-           "--row-align", str(args.row_align)]
+           "--row-align", str(args.row_align)] + (["--fused-gpx", "%.3f" % fused_gpx] if fused_gpx else [])
     env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "LOCAL_WORLD_SIZE")}
     r = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT, timeout=900)
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
@@ -1246,6 +1250,8 @@ def main():
                     help="batch and serve workloads: bytes every image row is padded to (input and output)")
     ap.add_argument("--quick", action="store_true", help="scene line only (no batch and serving summaries)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) leg")
+    ap.add_argument("--fused-gpx", type=float, default=0.0, help="serve workload: the fused single-scene rate "
+                                                                 "(Gpixel/s); adds a load offered at 80 %% of it")
     ap.add_argument("--height", type=int, default=0, help="single-image workloads: rows per band instead of the "
                                                           "workload's (a smaller case of it, e.g. for a profile)")
     ap.add_argument("--width", type=int, default=0, help="single-image workloads: columns instead of the workload's")
