@@ -328,3 +328,12 @@ def test_last_path_contract():
     t.join()
     assert seen == [(0, _lib.LUTC_PATH_AUTO), (0, _lib.LUTC_PATH_AUTO)]
     assert lib.lutc_last_path(None) == _lib.LUTC_EINVAL
+
+
+def test_fp64_probe_rejects_bad_arguments_before_launch():
+    lib = _lib.lib()
+    E = _lib.LUTC_EINVAL
+    assert lib.lutc_probe_fp64_fma(0, 10, ctypes.c_void_p(0x50000), None, None) == E
+    assert lib.lutc_probe_fp64_fma(4, 0, ctypes.c_void_p(0x50000), None, None) == E
+    assert lib.lutc_probe_fp64_fma(4, (1 << 24) + 1, ctypes.c_void_p(0x50000), None, None) == E
+    assert lib.lutc_probe_fp64_fma(4, 10, None, None, None) == E

@@ -118,3 +118,44 @@ def test_device_budget_that_cannot_be_allocated_is_refused():
     assert e.value.status == _lib.LUTC_ENOMEM
     x = torch.ones(1024, device="cuda")
     assert float(x.sum()) == 1024.0
+
+
+def test_replayed_schedule_on_the_device_equals_the_oracle():
+    # lutc_server_replay drives the real server: an open-loop schedule at a rate high enough to batch,
+    # every request's output equal to the oracle, the schedule kept, latency counted from the schedule
+    server = lutc.Server(budget_bytes=4 << 30, max_batch=8, max_wait_us=1000, streams=3)
+    pool = _setup(server)
+    rng = np.random.default_rng(7)
+    n = 120
+    at = np.cumsum(rng.exponential(1 / 3000.0, n))
+    reqs, expect = [], []
+    for i in range(n):
+        sid = int(rng.integers(0, len(SENSORS)))
+        h = int(rng.integers(1, 400))
+        p = pool[sid]
+        raw = p["draw"][:, :h].contiguous()
+        out = torch.full((p["bands"], h, p["w"]), 0xA5, dtype=torch.uint8, device="cuda")
+        reqs.append((float(at[i]), sid, raw, out, False))
+        expect.append((sid, h))
+    r = server.replay(reqs)
+    torch.cuda.synchronize()
+    assert (r["status"] == 0).all()
+    assert np.all(r["done_s"] >= r["scheduled_s"]) and np.all(np.diff(r["scheduled_s"]) >= 0)
+    assert r["batch_size"].max() > 1
+    for (sid, h), (_, _, _, out, _) in zip(expect, reqs):
+        np.testing.assert_array_equal(out.cpu().numpy(), _expected(pool[sid], h))
+    server.close()
+
+
+def test_fp64_probe_runs_and_counts_its_work():
+    import ctypes
+    lib = _lib.lib()
+    blocks, iters = 16, 64
+    sink = torch.zeros(blocks * 256, dtype=torch.float64, device="cuda")
+    fmas = ctypes.c_longlong(0)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.lutc_probe_fp64_fma(blocks, iters, ctypes.c_void_p(sink.data_ptr()), ctypes.byref(fmas), st) == 0
+    torch.cuda.synchronize()
+    assert fmas.value == blocks * 256 * 8 * iters
+    v = sink.cpu().numpy()
+    assert np.isfinite(v).all() and (v > 0).all()  # every thread wrote its chains' sum
