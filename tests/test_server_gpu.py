@@ -123,7 +123,8 @@ def test_device_budget_that_cannot_be_allocated_is_refused():
 def test_replayed_schedule_on_the_device_equals_the_oracle():
     # lutc_server_replay drives the real server: an open-loop schedule at a rate high enough to batch,
     # every request's output equal to the oracle, the schedule kept, latency counted from the schedule
-    server = lutc.Server(budget_bytes=4 << 30, max_batch=8, max_wait_us=1000, streams=3)
+    # every batch waits out a 1 ms window, so that requests share batches whatever the device's pace
+    server = lutc.Server(budget_bytes=4 << 30, max_batch=8, max_wait_us=1000, streams=3, hold_when_idle=True)
     pool = _setup(server)
     rng = np.random.default_rng(7)
     n = 120
