@@ -641,7 +641,8 @@ def run_large14(args):
 
 def served_summary(v, fused_value: float) -> dict:
     """The bench line's summary of the serving run (`--workload serve`)."""
-    keep = ("p50_ms", "p99_ms", "gpx_s", "req_s", "offered_req_s", "mean_batch", "requests", "failed", "tail")
+    keep = ("p50_ms", "p99_ms", "gpx_s", "req_s", "offered_req_s", "mean_batch", "requests", "failed", "tail",
+            "cache_misses")
     sat = v["saturation"]
     return {"saturation_gpx_s": sat["gpx_s"], "vs_fused_single": sat["gpx_s"] / fused_value,
             "saturation": {k: sat.get(k) for k in keep},
@@ -651,6 +652,7 @@ def served_summary(v, fused_value: float) -> dict:
                               "saturation": {k: v["host_requests"]["saturation"].get(k) for k in keep},
                               "latency_200": {k: v["host_requests"]["latency_200"].get(k) for k in keep},
                               "outputs_equal_single_calls": v["host_requests"]["outputs_equal_single_calls"]},
+            "first_requests": {k: v["warmup_with_cache_misses"].get(k) for k in keep},
             "load_generator": v["config"].get("load_generator"), "config": v["config"]["workload"]}
 
 
@@ -946,7 +948,12 @@ def run_serve(args):
                     submit_lag_max_ms=0.0 if closed else round(float(lag.max()) * 1e3, 3),
                     queue_ms=stage((r["start_s"] - r["submit_s"])[slow]), prep_ms=stage(prep[slow]),
                     launch_to_done_ms=stage(run[slow]), cache_misses=int(r["cache_miss"][slow].sum()))
+        miss = r["cache_miss"] == 1  # requests that uploaded their sensor's coefficients
+        misses = dict(requests=int(miss.sum()),
+                      p50_ms=float(np.percentile(lat[miss], 50) * 1e3) if miss.any() else None,
+                      max_ms=float(lat[miss].max() * 1e3) if miss.any() else None)
         return dict(p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=p99 * 1e3, gpx_s=px / span / 1e9,
+                    cache_misses=misses,
                     req_s=n / span, offered_req_s=None if closed else rate,
                     offered_gpx_s=None if closed else mean_px * rate / 1e9,
                     mean_batch=float(np.mean(r["batch_size"])), requests=n, failed=int((r["status"] != 0).sum()),

@@ -46,6 +46,7 @@ def test_served_summary_keeps_latency_beside_every_throughput():
     v = {"saturation": dict(load, gpx_s=900.0, offered_req_s=None), "latency": {"50": load, "75% of saturation": load},
          "outputs_equal_single_calls": True,
          "host_requests": {"saturation": dict(load, gpx_s=50.0), "latency_200": load, "outputs_equal_single_calls": True},
+         "warmup_with_cache_misses": dict(load, tail=dict(cache_misses=3)),
          "config": {"workload": "serve", "load_generator": "native"}}
     s = bench.served_summary(v, 1000.0)
     assert s["saturation_gpx_s"] == 900.0 and abs(s["vs_fused_single"] - 0.9) < 1e-12
