@@ -817,9 +817,9 @@ def run_batch(args):
     # (the device outputs are row-pitched views; their D2H copies go through torch's strided copy)
     e2e_ms = timed(e2e, 3)
 
-    # kernels one batch step launches (every image here takes the TMA kernels): pass 1 split into the
-    # images of <= 12 bits and the deeper ones, the scan, pass 2
-    batch_launches = int(any(im["bits"] <= 12 for im in ims)) + int(any(im["bits"] > 12 for im in ims)) + 2
+    # kernels one batch step launches (every image here takes the TMA kernels): the reset of histograms
+    # and runs, pass 1 split into the images of <= 12 bits and the deeper ones, the scan, pass 2
+    batch_launches = 1 + int(any(im["bits"] <= 12 for im in ims)) + int(any(im["bits"] > 12 for im in ims)) + 2
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
@@ -964,19 +964,24 @@ def run_serve(args):
     sat = drive(0, max(2000, 2 * args.steps), closed=True)
     loads = {}
     # the configured open-loop loads, at least 2000 requests each (40 s at 50 req/s)
+    # (`--cases` keeps only the loads whose names contain one of its words; saturation always runs)
     for rate, n in ((50, max(2000, args.steps // 4)), (200, max(2000, args.steps)), (800, max(2000, 2 * args.steps))):
-        loads[str(rate)] = drive(rate, n)
+        if _selected(args, str(rate)):
+            loads[str(rate)] = drive(rate, n)
     # loads high enough to batch for real: fractions of the saturated request rate, ~1 s each
     for frac in (0.25, 0.5, 0.75, 0.9):
-        rate = frac * sat["req_s"]
-        loads["%d%% of saturation" % round(100 * frac)] = drive(rate, int(max(2000, min(60000, rate))))
+        rate, name = frac * sat["req_s"], "%d%% of saturation" % round(100 * frac)
+        if _selected(args, name):
+            loads[name] = drive(rate, int(max(2000, min(60000, rate))))
     # the metric's own target: an offered load of 80 % of the fused single-scene rate, when it is known
-    if args.fused_gpx:
+    if args.fused_gpx and _selected(args, "80% of the fused scene"):
         rate = 0.8 * args.fused_gpx * 1e9 / mean_px
         loads["80% of the fused scene"] = drive(rate, int(max(2000, min(60000, rate))))
     # requests from pinned host memory: staged in and out by the server (copies inside each request's latency)
-    host_sat = drive(0, max(300, args.steps), closed=True, host=True)
-    host_200 = drive(200, max(300, args.steps // 2), host=True)
+    empty = dict(p50_ms=None, p99_ms=None, gpx_s=None, tail=None)
+    host = _selected(args, "host")
+    host_sat = drive(0, max(300, args.steps), closed=True, host=True) if host else empty
+    host_200 = drive(200, max(300, args.steps // 2), host=True) if host else empty
     host_exact = True
     for k in sorted(used_host)[::9]:  # entries some request wrote
         sid, raw_np, out_np = pool_host[k][:3]
@@ -1262,7 +1267,7 @@ def main():
     ap.add_argument("--height", type=int, default=0, help="single-image workloads: rows per band instead of the "
                                                           "workload's (a smaller case of it, e.g. for a profile)")
     ap.add_argument("--width", type=int, default=0, help="single-image workloads: columns instead of the workload's")
-    ap.add_argument("--cases", default="", help="fit / demosaic workloads: run only the cases whose name contains "
+    ap.add_argument("--cases", default="", help="fit / demosaic / serve workloads: run only the cases whose name contains "
                                                   "one of these comma-separated words ('_' stands for a space)")
     args = ap.parse_args()
     if args.workload == "batch" and args.impl != "reference":

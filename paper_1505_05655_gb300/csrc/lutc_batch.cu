@@ -8,15 +8,16 @@
 // about equal modelled cost (a strip row costs its valid columns plus one
 // full strip's width).  Sequence per run:
 //
-//   memset(histograms) -> pass 1 (stretch images of <= 12 bits) -> pass 1
+//   reset (histograms, runs) -> pass 1 (stretch images of <= 12 bits) -> pass 1
 //   (deeper ones: larger histograms, fewer blocks per SM) -> scan (one block
 //   per image band) -> pass 2 (all stretch images) -> detector-only pass (all
 //   uint16 images) -> images the TMA kernels cannot take, one by one
 //
-// The two pass-1 launches balance themselves at run time as well: each block
-// claims its run a granule at a time and, once done, steals the upper half of
-// the largest run left (lutc_tma.cu); the runs start from the planned
-// boundaries, copied into place on the device before each launch.
+// The pass launches balance themselves at run time as well: each block claims
+// its run a granule at a time and, once done, steals the upper half of the
+// largest run left (lutc_tma.cu); the runs start from the planned boundaries,
+// put back in place (with the histograms cleared) by one kernel at the start
+// of every run.
 //
 // optionally captured once in a CUDA graph and replayed (lutc_batch_correct:
 // planned, run once and released in one call).  All device data (job table,
@@ -102,6 +103,30 @@ struct Plan {
     size_t hist_bytes = 0, S_bytes = 0;
     int s_max_bits = 8, d_max_bits = 8;
 };
+
+// The start of every run: the stretch images' histograms cleared and each stealing launch's runs put
+// back at their planned starts (the previous run left them used up) -- one kernel, where a memset and
+// three copies would each leave a gap between the kernels around them.
+struct ResetArgs {
+    unsigned long long* hist;
+    size_t hist_words;
+    const uint64_t* init[kStealLaunches];
+    unsigned long long* live[kStealLaunches];
+    int count[kStealLaunches];
+};
+
+__global__ void __launch_bounds__(256) k_batch_reset(const ResetArgs a)
+{
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t nt = (size_t)gridDim.x * blockDim.x;
+    ulonglong2* h2 = reinterpret_cast<ulonglong2*>(a.hist);  // 256-byte aligned in the workspace
+    const size_t pairs = a.hist_words / 2;
+    for (size_t i = t; i < pairs; i += nt) h2[i] = make_ulonglong2(0ull, 0ull);
+    if (t == 0 && (a.hist_words & 1)) a.hist[a.hist_words - 1] = 0ull;
+#pragma unroll
+    for (int l = 0; l < kStealLaunches; ++l)
+        for (size_t i = t; i < (size_t)a.count[l]; i += nt) a.live[l][i] = a.init[l][i];
+}
 
 bool batch_tma_ok(const lutc_job& j)
 {
@@ -236,10 +261,25 @@ int enqueue(lutc_batch b, cudaStream_t st, cudaEvent_t* tr)
         L.S = b->ws + p.off_S;
         L.S_out = b->ws + p.off_S;
         L.unit_offset = 0;
-        if ((rc = cuda_status(cudaMemsetAsync(L.hist, 0, p.hist_bytes, st)))) return rc;
         // pass 1 in two launches: small histograms (more blocks per SM), then the rest
         const int64_t* part = reinterpret_cast<const int64_t*>(b->ws + p.off_part);
         uint64_t* steal = reinterpret_cast<uint64_t*>(b->ws + p.off_steal);  // [launch][initial | live][block]
+        {
+            ResetArgs ra;
+            ra.hist = L.hist;
+            ra.hist_words = p.hist_bytes / 8;
+            const bool runs[kStealLaunches] = {p.ns_small > 0, p.ns - p.ns_small > 0, true};
+            for (int l = 0; l < kStealLaunches; ++l) {
+                uint64_t* init = steal + (size_t)l * 2 * kMaxGrid;
+                ra.init[l] = init;
+                ra.live[l] = reinterpret_cast<unsigned long long*>(init + kMaxGrid);
+                ra.count[l] = (b->steal && runs[l]) ? b->grid[l] : 0;
+            }
+            const size_t pairs = ra.hist_words / 2;
+            const int blocks = (int)std::max<size_t>(1, std::min<size_t>((pairs + 255) / 256, (size_t)4 * sm_count()));
+            k_batch_reset<<<blocks, 256, 0, st>>>(ra);
+            if ((rc = cuda_status(cudaGetLastError()))) return rc;
+        }
         BatchLaunch L1 = L;
         L1.njobs = p.ns_small;
         L1.max_bits = b->small_max_bits;
@@ -258,14 +298,9 @@ int enqueue(lutc_batch b, cudaStream_t st, cudaEvent_t* tr)
         for (int l = 0; l < 2; ++l) {
             BatchLaunch& Lp = *P1[l];
             if (Lp.njobs <= 0) continue;
-            if (b->steal) {
-                // every run back at its planned start (the previous run left them used up)
-                uint64_t* init = steal + (size_t)l * 2 * kMaxGrid;
-                Lp.ranges = reinterpret_cast<unsigned long long*>(init + kMaxGrid);
+            if (b->steal) {  // runs reset by k_batch_reset above
+                Lp.ranges = reinterpret_cast<unsigned long long*>(steal + (size_t)l * 2 * kMaxGrid + kMaxGrid);
                 Lp.granule = b->granule[l];
-                if ((rc = cuda_status(cudaMemcpyAsync(Lp.ranges, init, sizeof(uint64_t) * Lp.grid,
-                                                      cudaMemcpyDeviceToDevice, st))))
-                    return rc;
             }
             if ((rc = tma_batch_pass(Lp, kModeHist, tc, bps, st))) return rc;
         }
@@ -277,12 +312,8 @@ int enqueue(lutc_batch b, cudaStream_t st, cudaEvent_t* tr)
         L.starts = part + 2 * (kMaxGrid + 1);
         L.grid = b->grid[2];
         if (b->steal) {
-            uint64_t* init = steal + (size_t)2 * 2 * kMaxGrid;
-            L.ranges = reinterpret_cast<unsigned long long*>(init + kMaxGrid);
+            L.ranges = reinterpret_cast<unsigned long long*>(steal + (size_t)2 * 2 * kMaxGrid + kMaxGrid);
             L.granule = b->granule[2];
-            if ((rc = cuda_status(cudaMemcpyAsync(L.ranges, init, sizeof(uint64_t) * L.grid, cudaMemcpyDeviceToDevice,
-                                                  st))))
-                return rc;
         }
         if ((rc = tma_batch_pass(L, kModeApplyStretch, tc, bps, st))) return rc;
     } else if (tr) {
