@@ -29,8 +29,9 @@ namespace lutc {
 
 bool tma_eligible(const lutc_raster* in);
 int tma_hist(const lutc_raster* in, const lutc_coeffs* per_band, unsigned long long* hist, cudaStream_t st);
+// programmatic: pass 2 launched right behind the scan of the same call (lutc_correct_image only)
 int tma_apply(const lutc_raster* in, const lutc_coeffs* per_band, const uint8_t* S, void* out, int64_t out_pitch,
-              bool stretch, cudaStream_t st);
+              bool stretch, cudaStream_t st, bool programmatic = false);
 
 namespace {
 
@@ -537,10 +538,14 @@ extern "C" int lutc_correct_image(const lutc_raster* in, const lutc_coeffs* per_
     if (tr) cudaEventRecord(tr[0], st);
     if ((rc = cuda_status(cudaMemsetAsync(hist, 0, (size_t)in->bands * L * 8, st)))) return rc;
     if (!empty && (rc = tma ? tma_hist(in, per_band, hist, st) : launch_hist(a, in, hist, st))) return rc;
+    // TMA path, untraced: the scan launches behind pass 1 and pass 2 behind the scan (programmatic
+    // launch), each waiting on the device for the data it reads -- pass 2's blocks start streaming
+    // raw tiles while the scan runs
+    const bool chain = tma && !tr;
     if (tr) cudaEventRecord(tr[1], st);
-    if ((rc = launch_stretch(hist, in->bands, in->bits, S, lohi, st))) return rc;
+    if ((rc = launch_stretch(hist, in->bands, in->bits, S, lohi, st, chain))) return rc;
     if (tr) cudaEventRecord(tr[2], st);
-    if (!empty && (rc = tma ? tma_apply(in, per_band, S, out, out_pitch_bytes, true, st)
+    if (!empty && (rc = tma ? tma_apply(in, per_band, S, out, out_pitch_bytes, true, st, chain)
                             : launch_apply<true>(a, in, S, out, out_pitch_bytes, st)))
         return rc;
     if (tr) cudaEventRecord(tr[3], st);

@@ -127,7 +127,29 @@ int tma_batch_pass(const BatchLaunch& b, int mode, int column_threads, int block
 // Stealing launches pack unit numbers in 32 bits: their units must stay below this.
 constexpr int64_t kStealMaxUnits = ((int64_t)1 << 32) - ((int64_t)1 << 20);
 int tma_batch_grid(int mode, int column_threads, int max_bits, int blocks_per_sm);
-int launch_stretch(const unsigned long long* hist, int bands, int bits, uint8_t* S, int32_t* lohi, cudaStream_t st);
+// programmatic: launched right behind pass 1 of the same stream, overlapping its tail (see launch_programmatic)
+int launch_stretch(const unsigned long long* hist, int bands, int bits, uint8_t* S, int32_t* lohi, cudaStream_t st,
+                   bool programmatic = false);
+
+// Launches `k` with the programmatic stream serialization attribute: it may start as soon as every
+// block of the previous kernel in the stream has signalled (ptx::launch_dependents) and must call
+// ptx::wait_prerequisites before it reads anything that kernel (or one before it) writes.  Used only
+// between kernels of the library's own sequences, whose data flow is known.
+template <class K, class... Args>
+cudaError_t launch_programmatic(K k, dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
 int stretch_batch(const TableDesc* tables, int ntables, const unsigned long long* hist, uint8_t* S, int32_t* lohi,
                   cudaStream_t st);
 enum { kModeHist = 0, kModeHistGlobal = 1, kModeApplyStretch = 2, kModeApplyDetector = 3 };

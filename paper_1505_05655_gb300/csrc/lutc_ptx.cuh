@@ -82,7 +82,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
-// orders this thread's generic-proxy shared-memory accesses before later async-proxy (TMA) writes
 // 1-D tiled tensor load; x * element size must be a multiple of 16 bytes (out-of-range reads fill zeros)
 __device__ __forceinline__ void tma_load_1d(void* dst, const CUtensorMap* map, uint64_t* bar, int x)
 {
@@ -92,9 +91,24 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// orders this thread's generic-proxy shared-memory accesses before later async-proxy (TMA) writes
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Programmatic dependent launch.  A kernel launched after this grid with the programmatic stream
+// serialization attribute may start once every block of this grid has executed this (or exited).
+__device__ __forceinline__ void launch_dependents()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Waits until the grids this one depends on programmatically have completed and their memory writes
+// are visible; returns at once in a grid launched without that attribute.
+__device__ __forceinline__ void wait_prerequisites()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 }  // namespace ptx

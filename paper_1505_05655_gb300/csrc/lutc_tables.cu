@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include "lutc_internal.cuh"
+#include "lutc_ptx.cuh"
 
 namespace lutc {
 namespace {
@@ -221,6 +222,10 @@ __device__ __forceinline__ void stretch_band_bits(const unsigned long long* __re
 __global__ void __launch_bounds__(kScanThreads) k_stretch(const unsigned long long* __restrict__ hist, int bits,
                                                           uint8_t* __restrict__ S, int32_t* __restrict__ lohi)
 {
+    // launched right behind pass 1 (programmatic launch): let pass 2 launch behind this grid, then wait
+    // for pass 1's histogram
+    ptx::launch_dependents();
+    ptx::wait_prerequisites();
     const int64_t L = (int64_t)1 << bits;
     const int b = blockIdx.x;
     stretch_band_bits(hist + b * L, bits, S + b * L, lohi + 2 * b);
@@ -291,10 +296,14 @@ int launch_apply_table(const lutc_raster* in, const OutT* table, void* out, int6
 
 }  // namespace
 
-int launch_stretch(const unsigned long long* hist, int bands, int bits, uint8_t* S, int32_t* lohi, cudaStream_t st)
+int launch_stretch(const unsigned long long* hist, int bands, int bits, uint8_t* S, int32_t* lohi, cudaStream_t st,
+                   bool programmatic)
 {
-    k_stretch<<<bands, kScanThreads, 0, st>>>(hist, bits, S, lohi);
-    return cuda_status(cudaGetLastError());
+    if (!programmatic) {
+        k_stretch<<<bands, kScanThreads, 0, st>>>(hist, bits, S, lohi);
+        return cuda_status(cudaGetLastError());
+    }
+    return cuda_status(launch_programmatic(k_stretch, dim3(bands), dim3(kScanThreads), 0, st, hist, bits, S, lohi));
 }
 
 int tables_preload()

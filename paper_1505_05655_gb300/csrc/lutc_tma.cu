@@ -335,6 +335,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
     uint32_t* hs = reinterpret_cast<uint32_t*>(table);
 
     const int tid = threadIdx.x;
+    // pass 1: the scan behind it may launch now (it waits for this grid's histogram itself)
+    if (MODE == kHist || MODE == kHistGlobal) ptx::launch_dependents();
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -525,6 +527,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_tma_strip(const __grid_constant
     }
 
     // ---------------------------------------------------------------- consumers
+    // pass 2 launched right behind the scan (programmatic launch): the producer already streams raw
+    // tiles, which no kernel of the step writes; the stretch table is read only after the scan
+    if constexpr (MODE == kApplyStretch) ptx::wait_prerequisites();
     const int ct = tid % TC;  // column thread: owns columns strip * SW + ct * 8 .. + 7
     const int ph = tid / TC;  // row phase
     const int lane = tid & 31;
@@ -779,7 +784,7 @@ int grid_for(K k, size_t smem, int blocks_per_sm, int64_t* grid)
 }
 
 template <int TC, int MODE>
-int launch_single_tc(TmaArgs& a, cudaStream_t st)
+int launch_single_tc(TmaArgs& a, cudaStream_t st, bool programmatic)
 {
     auto k = k_tma_strip<TC, MODE, false, TmaArgs>;
     const size_t smem = (size_t)kTableOffset + table_bytes(MODE, a.max_bits);
@@ -790,17 +795,18 @@ int launch_single_tc(TmaArgs& a, cudaStream_t st)
     a.job.strips = (a.job.W + SW - 1) / SW;
     a.units = (int64_t)a.job.bands * a.job.strips * a.job.H;
     a.units_per_block = (a.units + grid - 1) / grid;
+    if (programmatic) return cuda_status(launch_programmatic(k, dim3((unsigned)grid), dim3(kThreads), smem, st, a));
     k<<<(unsigned)grid, kThreads, smem, st>>>(a);
     return cuda_status(cudaGetLastError());
 }
 
 template <int MODE>
-int launch_single(TmaArgs& a, int tc, cudaStream_t st)
+int launch_single(TmaArgs& a, int tc, cudaStream_t st, bool programmatic = false)
 {
     switch (tc) {
-    case 256: return launch_single_tc<256, MODE>(a, st);
-    case 128: return launch_single_tc<128, MODE>(a, st);
-    default: return launch_single_tc<64, MODE>(a, st);
+    case 256: return launch_single_tc<256, MODE>(a, st, programmatic);
+    case 128: return launch_single_tc<128, MODE>(a, st, programmatic);
+    default: return launch_single_tc<64, MODE>(a, st, programmatic);
     }
 }
 
@@ -963,7 +969,7 @@ int tma_hist(const lutc_raster* in, const lutc_coeffs* per_band, unsigned long l
 }
 
 int tma_apply(const lutc_raster* in, const lutc_coeffs* per_band, const uint8_t* S, void* out, int64_t out_pitch,
-              bool stretch, cudaStream_t st)
+              bool stretch, cudaStream_t st, bool programmatic)
 {
     TmaArgs a;
     const int tc = pick_tc(in->width, in->bits);
@@ -974,7 +980,7 @@ int tma_apply(const lutc_raster* in, const lutc_coeffs* per_band, const uint8_t*
     const int64_t vec = stretch ? 8 : 16;
     a.job.vout = ((uintptr_t)out % vec == 0) && (out_pitch % vec == 0);
     a.S = S;
-    return stretch ? launch_single<kApplyStretch>(a, tc, st) : launch_single<kApplyDetector>(a, tc, st);
+    return stretch ? launch_single<kApplyStretch>(a, tc, st, programmatic) : launch_single<kApplyDetector>(a, tc, st);
 }
 
 int tma_batch_grid(int mode, int column_threads, int max_bits, int blocks_per_sm)
