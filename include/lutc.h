@@ -463,6 +463,11 @@ LUTC_API int lutc_batch_create(const lutc_job* jobs, int n, const lutc_batch_con
  * call captures this sequence in a CUDA graph (on an internal stream; make
  * that first call before capturing `stream` yourself) and every call
  * launches the graph.  Results equal lutc_correct_image on each image.
+ * The passes balance their blocks at run time (a block that finishes its
+ * planned share takes half of the largest share left); every run starts
+ * from the planned shares again.  Runs of one batch share its workspace
+ * (histograms, tables, the blocks' shares): runs that overlap on the GPU
+ * race, so enqueue them on one stream.
  */
 LUTC_API int lutc_batch_run(lutc_batch batch, lutc_stream stream);
 
