@@ -573,6 +573,7 @@ def finish_lutc(args, line, wl, rank, ws, raw_h, out_h, A, G, O, value):
         torch.cuda.empty_cache()
         # the large 14-bit scene on the same kernels, timed and checked against the oracle in full
         line["large14"] = run_large14(sub)
+        line["tiny"] = run_tiny(sub)
         gc.collect()
         torch.cuda.empty_cache()
         b = run_batch(sub)
@@ -636,6 +637,39 @@ def run_large14(args):
                                "sample": "the whole large14 workload on %d threads, %.1f s (inputs generated in "
                                          "%.1f s)" % (threads, dt, gen_s)}
     del raw, out, wsb
+    return res
+
+
+def run_tiny(args):
+    """The tiny detector-only configuration (1 x 1024 x 1024, 12-bit, uint16 out): graph-timed steps and
+    the output against the oracle."""
+    import torch
+    import synth
+    import paper_1505_05655_gb300 as lutc
+    import oracle
+
+    wl = synth.WORKLOADS["tiny"]
+    device = torch.device("cuda", torch.cuda.current_device())
+    lib = lutc.lib()
+    raw_np, A, G, O = gen_inputs(wl, 0)
+    raw = torch.from_numpy(raw_np).to(device)
+    dA, dG, dO = (torch.from_numpy(a).to(device) for a in (A, G, O))
+    out = torch.empty(raw.shape, dtype=torch.uint16, device=device)
+    desc = lutc.raster_desc(raw, wl.bits)
+    cd = lutc.coeff_descs(dA, dG, dO)
+    wsb = torch.empty(256, dtype=torch.uint8, device=device)
+    steps = 2000
+    leg = fused_leg(lib, lutc, wl, raw, cd, out, wsb, device, steps, 10)
+    ms_step = leg["ms"] / steps
+    res = {"config": workload_config(wl), "steps": steps, "us_per_step": ms_step * 1e3,
+           "value": wl.pixels / (ms_step * 1e-3) / 1e9, "unit": UNIT,
+           "kernel_family": {1: "tma", 2: "strip"}.get(leg["path"], "none"),
+           "timing": "CUDA events around %d replays of a CUDA graph holding one call; 4 MB in and out, inside L2 "
+                     "(launch-bound: reported, not held against the HBM roofline)" % steps}
+    if not args.no_cpu_baseline:
+        ref = oracle.correct_image(raw_np, A, G, O, wl.bits, stretch=False)
+        res["parity"] = {"bit_exact_vs_oracle": bool(np.array_equal(ref, out.cpu().numpy())),
+                         "pixels_compared": int(ref.size)}
     return res
 
 

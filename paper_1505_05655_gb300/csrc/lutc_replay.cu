@@ -7,7 +7,7 @@
 // the latency is counted from that scheduled time, so that a late hand-over
 // shows up as the generator's lateness (submit_s - scheduled) and never
 // hides inside the server's figure.  Here one native thread submits on
-// schedule (it sleeps until ~0.2 ms before a request is due, then spins) and
+// schedule (it sleeps until ~2 ms before a request is due, then spins) and
 // the calling thread collects the tickets in order; no interpreter lock or
 // garbage collector of the caller sits between the two.  Host code only.
 #include <algorithm>
@@ -25,7 +25,8 @@ double steady_s()
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-constexpr double kSpinWindow = 200e-6;     // spin, rather than sleep, this close to a due time
+constexpr double kSpinWindow = 2e-3;       // spin, rather than sleep, this close to a due time (a sleep on a
+                                           // busy host can end a millisecond or more late)
 constexpr double kBusyRetry = 20e-6;       // a queue-full refusal (closed bursts) is retried this often
 constexpr double kGiveUp = 120.0;          // longest a submit may keep being refused, or a ticket may run
 constexpr int64_t kWaitSliceUs = 1000000;  // one lutc_server_wait call (re-issued until kGiveUp)
