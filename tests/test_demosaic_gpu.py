@@ -1,8 +1,8 @@
 """Parity of the CUDA bilinear demosaic with the oracle (GPU).
 
 Integer arithmetic throughout: tolerance zero.  Shapes span several tiles
-(128 x 64 on the TMA-fed path, 128 x 16 or 128 x 32 on the plain one) with
-ragged right and bottom edges, tiles whose halo leaves the image,
+(128 x 32 or 128 x 64 on the TMA-fed path, which raw frames take above 4 M
+pixels; 128 x 16 or 128 x 32 on the plain one) with ragged right and bottom edges, tiles whose halo leaves the image,
 degenerate images one pixel wide or high, unaligned rows on both sides, coefficient
 rows off a 16-byte boundary (no TMA staging of the coefficients), all
 four CFA patterns, with and without the fused detector correction (int32 and
@@ -132,6 +132,17 @@ def test_unaligned_coefficient_rows(coef_off):
         out = lutc.demosaic(torch.from_numpy(img).cuda(), pattern, bits, A=shifted(A), G=shifted(G), O=shifted(O))
         torch.cuda.synchronize()
         np.testing.assert_array_equal(out.cpu().numpy(), _ref(img, w, pattern, bits, (A, G, O)))
+
+
+@pytest.mark.parametrize("h,w,pad", [(2050, 2048, 0), (1031, 4104, 8), (2100, 2000, 0)])
+def test_raw_frames_above_4m_pixels_take_the_tma_kernel(h, w, pad):
+    # raw frames of more than 4 M pixels with aligned rows run the TMA-fed persistent kernel (smaller
+    # raw frames the block-per-tile one): ragged in both directions, every pattern, 16-bit
+    assert h * w > (1 << 22)
+    img = _raw(60 + h, h, w, 16, pad=pad)
+    assert (img.strides[0] % 16) == 0
+    for pattern in PATTERNS:
+        np.testing.assert_array_equal(_gpu(img, w, pattern, 16), _ref(img, w, pattern, 16))
 
 
 def test_paper_frame_2048_16bit():
