@@ -326,6 +326,31 @@ def test_every_launch_configuration_is_exact(path, column_threads):
             lutc.reset_tuning(bits)
 
 
+@pytest.mark.parametrize("column_threads", [64, 128, 256])
+def test_rasters_with_fewer_tiles_than_a_wave(column_threads):
+    """TMA passes on rasters with fewer tiles of work than one wave of blocks: the grid shrinks to the
+    tiles (one tile of rows per block, the last share ragged), down to a single block; every result
+    equals the oracle's."""
+    cases = [(1, 1, 256, 12), (1, 5, 1024, 12), (2, 3, 2048, 10), (3, 17, 4096, 14), (1, 9, 16384, 12),
+             (4, 33, 800, 12), (1, 64, 520, 13)]
+    try:
+        for bands, h, w, bits in cases:
+            lutc.set_tuning(bits, path=1, column_threads=column_threads)
+            raw, A, G, O = make_case(1700 + h * w + column_threads, bands, h, w, bits, sat=0.01)
+            dr, dA, dG, dO = dev(raw), dev(A), dev(G), dev(O)
+            out, (hist, S, lohi) = lutc.correct_image(dr, dA, dG, dO, bits, with_tables=True)
+            assert lutc.last_path() == _lib.LUTC_PATH_TMA
+            ref, (rh, rS, rl) = oracle.correct_image(raw, A, G, O, bits, with_tables=True)
+            np.testing.assert_array_equal(host(hist), rh, err_msg=str((bands, h, w, bits)))
+            np.testing.assert_array_equal(host(lohi), rl)
+            np.testing.assert_array_equal(host(out), ref, err_msg=str((bands, h, w, bits)))
+            np.testing.assert_array_equal(host(lutc.correct_image(dr, dA, dG, dO, bits, stretch=False)),
+                                          oracle.correct_image(raw, A, G, O, bits, stretch=False))
+    finally:
+        for bits in (10, 12, 13, 14):
+            lutc.reset_tuning(bits)
+
+
 def test_a_wait_that_runs_out_is_reported_and_the_device_stays_usable():
     # a barrier nobody completes, with a limit of 2 M cycles (~1 ms): the wait gives up, records
     # LUTC_ETIMEOUT in the status word and the block returns
