@@ -369,6 +369,9 @@ enum { LUTC_BAYER_RGGB = 0, LUTC_BAYER_BGGR = 1, LUTC_BAYER_GRBG = 2, LUTC_BAYER
  *     aligned rows take vector stores.
  * Returns LUTC_EINVAL for a bad raster, pattern, output or coefficient set
  * before any launch; an empty raster returns LUTC_OK with nothing launched.
+ * LUTC_EUNSUPPORTED, before any launch, for a frame of more than 1 048 560
+ * rows that the persistent TMA-fed kernel does not take (rows not 16-byte
+ * aligned, fewer than 144 columns, or a raw frame of at most 4 M pixels).
  * Asynchronous on `stream`.
  */
 LUTC_API int lutc_demosaic(const lutc_raster* in, const lutc_coeffs* coeffs, int pattern, uint16_t* out,
