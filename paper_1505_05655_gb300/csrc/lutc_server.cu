@@ -130,6 +130,7 @@ struct Flight {
     size_t ws_off = 0, ws_bytes = 0;
     lutc_batch batch = nullptr;
     double t_ready = 0;  // fake executor
+    double t_launched = 0;
     int status = LUTC_OK;
 };
 
@@ -430,6 +431,7 @@ void lutc_server_st::run_batcher()
         const double t1 = now_s();
         lk.lock();
         for (Request* r : f->reqs) r->t_launched = t1;
+        f->t_launched = t1;
         // an uploaded sensor stays cached even if its batch failed later; after a failed upload
         // (no kernel of this batch was launched) its memory is returned and the next request retries
         for (Sensor* sp : up) {
@@ -469,6 +471,10 @@ void lutc_server_st::run_completer()
     // sleep lasts ~60 us, and that delay would land on every request's latency
     prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);
 #endif
+    // within kSpinWindow of the newest launch the thread polls every ~2 us without sleeping (a lone
+    // request's kernels take tens of microseconds: a 10 us sleep would add ~5 us to it on average);
+    // later, and while nothing runs, it sleeps
+    constexpr double kSpinWindow = 300e-6, kSpinPause = 2e-6;
     std::unique_lock<std::mutex> lk(mu);
     for (;;) {
         cv_done.wait(lk, [&] { return stop_completer || !flights.empty(); });
@@ -505,8 +511,16 @@ void lutc_server_st::run_completer()
             cv_wait.notify_all();
             cv_batcher.notify_all();
         } else {
+            double newest = 0;
+            for (const Flight* f : flights) newest = std::max(newest, f->t_launched);
+            const double t = now_s();
             lk.unlock();
-            std::this_thread::sleep_for(std::chrono::microseconds(10));
+            if (!cfg.fake_device && t - newest < kSpinWindow) {
+                while (now_s() - t < kSpinPause) {
+                }
+            } else {
+                std::this_thread::sleep_for(std::chrono::microseconds(10));
+            }
             lk.lock();
         }
     }
